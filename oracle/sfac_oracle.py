@@ -13,8 +13,9 @@ against the paper by eye:
   display of that label, Sec. 2.1);
 * the circulant and skew-circulant parts C and S of B entry by entry (eqs. (C),
   (S), Sec. 2.2);
-* matrix exponentials of the symmetric matrices C and S from a symmetric
-  eigendecomposition (a library primitive), exp(tM) = V diag(exp(t w)) V^T;
+* matrix exponentials of the symmetric matrices C and S by scaling and squaring
+  (scipy.linalg.expm, a library primitive); a second evaluation from a symmetric
+  eigendecomposition, exp(tM) = V diag(exp(t w)) V^T, serves as a cross-check;
 * the per-axis linear factor P = e^{tau/2 C} e^{tau S} e^{tau/2 C} (eq. (hatv)); by
   the Kronecker-sum form of C_alpha and S_alpha (eq. (newlinear)) the d-dimensional
   operator is the tensor product of the per-axis factors, applied line by line;
@@ -23,6 +24,17 @@ against the paper by eye:
   half flows between steps;
 * the one-level Strang step with the exact e^{tau B} per axis (eq. (strang)) and
   the splitting-ADI step of Sec. 5, which the paper compares against.
+
+Two evaluation routes of the same two-level factors exist. The "dense" route
+multiplies every line by the dense n x n matrix P (the definition). The
+"spectral" route applies e^{tau/2 C}, e^{tau S}, e^{tau/2 C} one after another
+through the diagonalisations of Remark 1 (C = F^* Lambda_C F and
+S = Theta^{-1} F^* Lambda_S F Theta) with numpy's FFT as the library primitive.
+The two agree to about 1e-13 per application (pinned). The spectral route
+exists because a dense FP64 matrix carries a fixed rounding error of a few
+1e-15 per application at n = 1024 (checked against a 30-digit evaluation);
+repeated for 1000 steps that error alone exceeds a 1e-12 comparison, whereas
+the spectral route stays near 1e-15 per application.
 
 Memory layout: a field is a numpy array of shape (n_d, ..., n_2, n_1), axis 1
 (x^(1)) fastest, which is the paper's lexicographic ordering (Sec. 2.1).
@@ -122,8 +134,15 @@ def split_CS(B: np.ndarray):
 # Flows (Sec. 2.2)
 # --------------------------------------------------------------------------
 
+def expm_dense(M: np.ndarray, t: float) -> np.ndarray:
+    """exp(t M) by scaling and squaring with Pade approximants (scipy.linalg.expm)."""
+    import scipy.linalg
+    return scipy.linalg.expm(t * M)
+
+
 def expm_symmetric(M: np.ndarray, t: float) -> np.ndarray:
-    """exp(t M) for symmetric M from its eigendecomposition M = V diag(w) V^T."""
+    """exp(t M) for symmetric M from its eigendecomposition M = V diag(w) V^T
+    (cross-check of expm_dense)."""
     w, V = np.linalg.eigh(M)
     return (V * np.exp(t * w)) @ V.T
 
@@ -137,15 +156,15 @@ def nonlinear_flow(v: np.ndarray, s: float) -> np.ndarray:
 def axis_two_level_factor(alpha: float, eps: float, h: float, n: int, tau: float) -> np.ndarray:
     """P = e^{tau/2 C} e^{tau S} e^{tau/2 C} for one axis (eq. (hatv))."""
     C, S = split_CS(matrix_B(alpha, eps, h, n))
-    EC = expm_symmetric(C, 0.5 * tau)
-    ES = expm_symmetric(S, tau)
+    EC = expm_dense(C, 0.5 * tau)
+    ES = expm_dense(S, tau)
     return EC @ ES @ EC
 
 
 def axis_one_level_factor(alpha: float, eps: float, h: float, n: int, tau: float) -> np.ndarray:
     """e^{tau B} for one axis; the d-dim e^{tau A} is their tensor product (eqs. (2DA),
     (3DA), (linear_operator))."""
-    return expm_symmetric(matrix_B(alpha, eps, h, n), tau)
+    return expm_dense(matrix_B(alpha, eps, h, n), tau)
 
 
 def axis_adi_factor(alpha: float, eps: float, h: float, n: int, tau: float) -> np.ndarray:
@@ -162,34 +181,72 @@ def apply_axis(u: np.ndarray, P: np.ndarray, axis: int) -> np.ndarray:
     return np.moveaxis(np.tensordot(P, u, axes=([1], [ax])), 0, ax)
 
 
+class SpectralFactor:
+    """e^{tau/2 C} e^{tau S} e^{tau/2 C} of one axis applied through Remark 1:
+    e^{t C} = F^{-1} diag(e^{t lambda}) F with lambda = F c (first column of C), and
+    e^{t S} = Theta^{-1} F^{-1} diag(e^{t mu}) F Theta with Theta = diag(e^{i pi k/n})
+    and mu = F (Theta s). F is numpy's forward FFT (e^{-2 pi i jk/n})."""
+
+    def __init__(self, alpha: float, eps: float, h: float, n: int, tau: float):
+        C, S = split_CS(matrix_B(alpha, eps, h, n))
+        self.theta = np.exp(1j * np.pi * np.arange(n) / n)
+        self.lam = np.fft.fft(C[:, 0]).real      # C symmetric: real spectrum
+        self.mu = np.fft.fft(self.theta * S[:, 0]).real
+        self.eC = np.exp(0.5 * tau * self.lam)
+        self.eS = np.exp(tau * self.mu)
+
+    def apply(self, u: np.ndarray, axis: int) -> np.ndarray:
+        """Multiply every line of u along paper axis `axis` (1-based)."""
+        ax = u.ndim - axis
+        shp = [1] * u.ndim
+        shp[ax] = -1
+        eC, eS, th = self.eC.reshape(shp), self.eS.reshape(shp), self.theta.reshape(shp)
+        z = np.fft.ifft(eC * np.fft.fft(u, axis=ax), axis=ax)
+        z = np.conj(th) * np.fft.ifft(eS * np.fft.fft(th * z, axis=ax), axis=ax)
+        z = np.fft.ifft(eC * np.fft.fft(z, axis=ax), axis=ax)
+        return z.real
+
+
 class Scheme:
-    """Per-axis dense factors for one problem (alpha per axis, eps, tau, [a, b]).
+    """Per-axis factors for one problem (alpha per axis, eps, tau, [a, b]).
 
     kind = "two_level" (eq. (finalstrang)), "one_level" (eq. (strang)) or "adi"
-    (the splitting-ADI scheme of Sec. 5).
+    (the splitting-ADI scheme of Sec. 5). route = "dense" multiplies lines by the
+    dense factor; route = "spectral" (two-level only) applies the factor through
+    Remark 1 (SpectralFactor).
     """
 
     def __init__(self, n: Sequence[int], alpha: Sequence[float], eps: float, tau: float,
-                 a: float = -1.0, b: float = 1.0, kind: str = "two_level"):
+                 a: float = -1.0, b: float = 1.0, kind: str = "two_level", route: str = "dense"):
         self.n = tuple(int(v) for v in n)
         self.alpha = tuple(float(v) for v in alpha)
         self.eps, self.tau, self.a, self.b = float(eps), float(tau), float(a), float(b)
-        build = {"two_level": axis_two_level_factor, "one_level": axis_one_level_factor,
-                 "adi": axis_adi_factor}[kind]
+        self.route = route
+        if route == "spectral":
+            if kind != "two_level":
+                raise ValueError("the spectral route evaluates the two-level factors only")
+            build = SpectralFactor
+        else:
+            build = {"two_level": axis_two_level_factor, "one_level": axis_one_level_factor,
+                     "adi": axis_adi_factor}[kind]
         self.P = []
         for ax, nn in enumerate(self.n):
             h = (self.b - self.a) / (nn + 1)
             self.P.append(build(self.alpha[ax], self.eps, h, nn, self.tau))
 
     @classmethod
-    def for_problem(cls, problem, kind: str = "two_level") -> "Scheme":
-        return cls(problem.n, problem.alpha, problem.eps, problem.tau, problem.a, problem.b, kind)
+    def for_problem(cls, problem, kind: str = "two_level", route: str = "dense") -> "Scheme":
+        return cls(problem.n, problem.alpha, problem.eps, problem.tau, problem.a, problem.b, kind, route)
+
+    def apply_linear(self, u: np.ndarray, axis: int) -> np.ndarray:
+        P = self.P[axis - 1]
+        return P.apply(u, axis) if self.route == "spectral" else apply_axis(u, P, axis)
 
     def step(self, u: np.ndarray) -> np.ndarray:
         """One step u <- J^Q_{tau/2} (prod_l P_l) J^Q_{tau/2} u (eqs. (strang), (finalstrang))."""
         u = nonlinear_flow(u, 0.5 * self.tau)
-        for ax, P in enumerate(self.P):
-            u = apply_axis(u, P, ax + 1)
+        for ax in range(len(self.P)):
+            u = self.apply_linear(u, ax + 1)
         return nonlinear_flow(u, 0.5 * self.tau)
 
     def run(self, u0: np.ndarray, nsteps: int) -> np.ndarray:
@@ -200,9 +257,10 @@ class Scheme:
         return u
 
 
-def solve(problem, u0: np.ndarray, nsteps: int | None = None, kind: str = "two_level") -> np.ndarray:
+def solve(problem, u0: np.ndarray, nsteps: int | None = None, kind: str = "two_level",
+          route: str = "dense") -> np.ndarray:
     """Run `nsteps` (default problem.steps) steps of the chosen scheme from u0."""
-    sch = Scheme.for_problem(problem, kind)
+    sch = Scheme.for_problem(problem, kind, route)
     return sch.run(u0, problem.steps if nsteps is None else nsteps)
 
 

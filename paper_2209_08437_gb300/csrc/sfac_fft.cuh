@@ -1,0 +1,175 @@
+// sfac_fft.cuh - device building blocks of the fused axis passes: complex
+// arithmetic, small in-register DFTs and a register-resident Stockham FFT.
+//
+// The linear flow of the two-level scheme applies, along every grid line of an
+// axis, e^{tau/2 C} e^{tau S} e^{tau/2 C} with C circulant and S skew-circulant
+// (eq. (hatv), Sec. 2.2). Remark 1 diagonalises both with the Fourier matrix:
+// C = F^* Lambda_C F and S = Theta^{-1} F^* Lambda_S F Theta with the twist
+// Theta = diag(e^{i pi k / n}). So each factor is FFT -> diagonal multiply ->
+// inverse FFT, and the S factor sits between the twist and its inverse.
+//
+// FFT organisation (written for this library). A line of N complex values is
+// held by T = N / E threads, thread t holding elements t + e*T, e in [0, E).
+// The transform runs as passes of a self-sorting (Stockham) decimation-in-time
+// FFT: a pass with current span P and radix RAD does N / RAD butterflies; the
+// butterfly i (k = i mod P) reads elements i + r N/RAD, multiplies input r by
+// w^{r k} with w = e^{-2 pi i / (P RAD)}, does a RAD-point DFT and writes output
+// r to position (i - k) RAD + k + r P. Thread t owns butterflies t + q T, whose
+// inputs are exactly its registers, so only the outputs of non-final passes go
+// through shared memory. In the final pass P = N / RAD, the outputs land on
+// positions t + e T again: the transform starts and ends in the same register
+// distribution, in natural order, and the diagonal multiplies that follow need
+// no reordering.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sfac {
+
+template <typename R>
+struct C2 {
+    R x, y;
+};
+
+template <typename R>
+__device__ __forceinline__ C2<R> cadd(C2<R> a, C2<R> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename R>
+__device__ __forceinline__ C2<R> csub(C2<R> a, C2<R> b) { return {a.x - b.x, a.y - b.y}; }
+// a * b
+template <typename R>
+__device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename R>
+__device__ __forceinline__ C2<R> cmulc(C2<R> a, C2<R> b) {
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+
+// cos(pi/8), sin(pi/8), sqrt(1/2) to 20 digits.
+#define SFAC_C8 0.92387953251128675613
+#define SFAC_S8 0.38268343236508977173
+#define SFAC_R2 0.70710678118654752440
+
+// x * e^{-+ 2 pi i q / 16} (forward: minus sign; INV: plus sign), q in [0, 8).
+// q is a compile-time constant after unrolling, so the branches fold away and
+// the multiplications by 1, -i and (1 -+ i)/sqrt 2 cost no general complex product.
+template <typename R, bool INV>
+__device__ __forceinline__ C2<R> rot16(C2<R> v, int q) {
+    const R c8 = R(SFAC_C8), s8 = R(SFAC_S8), r2 = R(SFAC_R2);
+    if (q == 0) return v;
+    if (q == 4) return INV ? C2<R>{-v.y, v.x} : C2<R>{v.y, -v.x};
+    if (q == 2) return INV ? C2<R>{r2 * (v.x - v.y), r2 * (v.x + v.y)}
+                           : C2<R>{r2 * (v.x + v.y), r2 * (v.y - v.x)};
+    if (q == 6) return INV ? C2<R>{-r2 * (v.x + v.y), r2 * (v.x - v.y)}
+                           : C2<R>{r2 * (v.y - v.x), -r2 * (v.x + v.y)};
+    R co, si;  // cos and sin of 2 pi q / 16 for odd q
+    if (q == 1) { co = c8; si = s8; }
+    else if (q == 3) { co = s8; si = c8; }
+    else if (q == 5) { co = -s8; si = c8; }
+    else { co = -c8; si = s8; }
+    return INV ? C2<R>{v.x * co - v.y * si, v.y * co + v.x * si}
+               : C2<R>{v.x * co + v.y * si, v.y * co - v.x * si};
+}
+
+// In-register M-point DFT (M = 1, 2, 4, 8, 16), natural order in and out:
+// y_s = sum_r x_r e^{-+2 pi i r s / M}. Radix-2 decimation in time.
+template <typename R, int M, bool INV>
+struct Dft {
+    static __device__ __forceinline__ void run(C2<R>* x) {
+        C2<R> ev[M / 2], od[M / 2];
+#pragma unroll
+        for (int i = 0; i < M / 2; ++i) {
+            ev[i] = x[2 * i];
+            od[i] = x[2 * i + 1];
+        }
+        Dft<R, M / 2, INV>::run(ev);
+        Dft<R, M / 2, INV>::run(od);
+#pragma unroll
+        for (int s = 0; s < M / 2; ++s) {
+            const C2<R> w = rot16<R, INV>(od[s], s * (16 / M));
+            x[s] = cadd(ev[s], w);
+            x[s + M / 2] = csub(ev[s], w);
+        }
+    }
+};
+template <typename R, bool INV>
+struct Dft<R, 1, INV> {
+    static __device__ __forceinline__ void run(C2<R>*) {}
+};
+
+// Exchange buffer of one line in shared memory. IDX_MAJOR interleaves the
+// lines of a CTA element by element (lanes of a warp walk over lines: the
+// strided-axis mapping); otherwise lines are stored one after another with a
+// pad of PAD elements (lanes walk along a line: the contiguous-axis mapping).
+template <typename R, int N, int LPC, bool IDX_MAJOR, int PAD>
+struct Exchange {
+    C2<R>* base;
+    int j;
+    __device__ __forceinline__ void put(int idx, C2<R> v) const {
+        if (IDX_MAJOR) base[idx * LPC + j] = v;
+        else base[j * (N + PAD) + idx] = v;
+    }
+    __device__ __forceinline__ C2<R> get(int idx) const {
+        return IDX_MAJOR ? base[idx * LPC + j] : base[j * (N + PAD) + idx];
+    }
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+    static constexpr int elems() { return IDX_MAJOR ? N * LPC : LPC * (N + PAD); }
+};
+
+// One Stockham pass (span P) and, recursively, the ones after it.
+// tw[m] = e^{-2 pi i m / N}, m in [0, N).
+template <typename R, int N, int E, int P, bool INV>
+struct FftPass {
+    static constexpr int RAD = (P * E <= N) ? E : (N / P);
+    static constexpr bool LAST = (P * RAD == N);
+    static constexpr int T = N / E;
+    static constexpr int Q = E / RAD;
+    static_assert(RAD >= 2 && (RAD & (RAD - 1)) == 0 && RAD <= 16, "radix");
+
+    template <class Ex>
+    static __device__ __forceinline__ void run(C2<R> (&x)[E], int t, const C2<R>* __restrict__ tw,
+                                               const Ex& ex) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int i = t + q * T;
+            const int k = i & (P - 1);
+            C2<R> a[RAD];
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) a[r] = x[q + r * Q];
+            if constexpr (P > 1) {
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    const C2<R> w = tw[r * k * (N / (P * RAD))];
+                    a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
+                }
+            }
+            Dft<R, RAD, INV>::run(a);
+            if constexpr (LAST) {
+#pragma unroll
+                for (int r = 0; r < RAD; ++r) x[q + r * Q] = a[r];
+            } else {
+                const int j = (i - k) * RAD + k;
+#pragma unroll
+                for (int r = 0; r < RAD; ++r) ex.put(j + r * P, a[r]);
+            }
+        }
+        if constexpr (!LAST) {
+            Ex::sync();
+#pragma unroll
+            for (int e = 0; e < E; ++e) x[e] = ex.get(t + e * T);
+            Ex::sync();
+            FftPass<R, N, E, P * RAD, INV>::run(x, t, tw, ex);
+        }
+    }
+};
+
+// Unnormalised FFT of one line held as described above (INV: inverse, no 1/N).
+template <typename R, int N, int E, bool INV, class Ex>
+__device__ __forceinline__ void line_fft(C2<R> (&x)[E], int t, const C2<R>* __restrict__ tw,
+                                         const Ex& ex) {
+    FftPass<R, N, E, 1, INV>::run(x, t, tw, ex);
+}
+
+}  // namespace sfac

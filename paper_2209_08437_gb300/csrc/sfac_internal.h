@@ -1,0 +1,43 @@
+// sfac_internal.h - declarations shared by the host side of libsfac and the
+// kernel translation units. Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace sfac {
+
+// Arguments of one fused axis pass over the field (see sfac_pass.cuh).
+//
+// The field is viewed along the pass axis as [outer][N][inner] reals:
+// element k of the line (o, i) sits at (o * N + k) * inner + i.
+//  - contiguous pass (inner == 1): real lines are the `outer` rows; rows 2c and
+//    2c+1 form complex line c (the odd last row, if any, pairs with zeros);
+//  - strided pass (inner > 1, even): columns 2c and 2c+1 of one outer slab form
+//    complex line c, read and written as one 2-real vector.
+// Tables (device pointers, plan precision R):
+//  eC[j]  = e^{tau/2 lambda_j} / N   circulant factor incl. the inverse-FFT 1/N
+//  eS[j]  = e^{tau mu_j} / N         skew-circulant factor incl. 1/N
+//  twist  = N complex e^{i pi k / N} (interleaved re, im)
+//  twid   = N complex e^{-2 pi i m / N}
+// J^Q_s(v) = v / sqrt(E + (1 - E) v^2) with E = e^{-2 s} is applied to every
+// value on load when jq_in != 0 and on store when jq_out != 0.
+struct PassArgs {
+    void* u;
+    long long outer;
+    long long inner;
+    long long clines;  // number of complex lines
+    const void* eC;
+    const void* eS;
+    const void* twist;
+    const void* twid;
+    double jq_in_E, jq_in_1mE;
+    double jq_out_E, jq_out_1mE;
+    int jq_in, jq_out;
+};
+
+// Launch one pass for line length N (a power of two in [4, 4096]).
+// Returns cudaErrorInvalidValue for an unsupported N.
+cudaError_t launch_pass_f64(int N, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_pass_f32(int N, const PassArgs& a, cudaStream_t s);
+
+}  // namespace sfac

@@ -1,0 +1,439 @@
+// sfac_plan.cu - host side of libsfac: parameter checks, the FP64 precompute of
+// the per-axis tables, the device plan and the C ABI declared in sfac.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sfac.h"
+#include "sfac_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sfac_status fail(sfac_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+sfac_status cuda_fail(cudaError_t err, const char* what) {
+    return fail(SFAC_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// ---------------------------------------------------------------------------
+// FP64 precompute (Sec. 2.1, Sec. 2.2, Remark 1)
+// ---------------------------------------------------------------------------
+
+// cos(pi m / n) and sin(pi m / n) for integer m, reduced exactly to an angle in
+// [0, pi/4] first so that every table entry is correctly rounded or nearly so.
+void sincospi_frac(long long m, long long n, double* c, double* s) {
+    const long long two_n = 2 * n;
+    m %= two_n;
+    if (m < 0) m += two_n;
+    double sc = 1.0, ss = 1.0;
+    if (m >= n) {  // theta - pi
+        m -= n;
+        sc = -sc;
+        ss = -ss;
+    }
+    if (2 * m > n) {  // pi - theta
+        m = n - m;
+        sc = -sc;
+    }
+    // theta = pi m / n in [0, pi/2]
+    double cv, sv;
+    if (4 * m > n) {  // theta = pi/2 - phi, phi = pi (n - 2m) / (2n) in [0, pi/4)
+        const double phi = M_PI * (double)(n - 2 * m) / (double)(2 * n);
+        cv = std::sin(phi);
+        sv = std::cos(phi);
+    } else {
+        const double th = M_PI * (double)m / (double)n;
+        cv = std::cos(th);
+        sv = std::sin(th);
+    }
+    *c = sc * cv;
+    *s = ss * sv;
+}
+
+// Compensated (Neumaier) summation.
+struct KahanSum {
+    double s = 0.0, c = 0.0;
+    void add(double v) {
+        const double t = s + v;
+        if (std::fabs(s) >= std::fabs(v)) c += (s - t) + v;
+        else c += (v - t) + s;
+        s = t;
+    }
+    double value() const { return s + c; }
+};
+
+struct AxisHost {
+    int n = 0;
+    std::vector<double> bcol, cfirst, sfirst, lambda, mu;
+    std::vector<double> eC, eS, twist, twid;  // twist, twid: interleaved complex
+};
+
+// Tables of one axis: omega_k by eqs. (g_coe), (omega_coe); b_k by eq. (B);
+// c_k, s_k by eqs. (C), (S); spectra by Remark 1; exponentials for tau.
+void compute_axis(double alpha, double eps, double tau, double a, double b, int n, AxisHost* T) {
+    T->n = n;
+    const double h = (b - a) / (double)(n + 1);
+    // g_{k+1} = (1 - (alpha+1)/(k+1)) g_k; omega_0 = alpha/2 g_0;
+    // omega_{k+1} = alpha/2 g_{k+1} + (2-alpha)/2 g_k
+    std::vector<double> g(n + 2), w(n + 2);
+    g[0] = 1.0;
+    for (int k = 0; k + 1 < n + 2; ++k) g[k + 1] = (1.0 - (alpha + 1.0) / (double)(k + 1)) * g[k];
+    w[0] = 0.5 * alpha * g[0];
+    for (int k = 0; k + 1 < n + 2; ++k) w[k + 1] = 0.5 * alpha * g[k + 1] + 0.5 * (2.0 - alpha) * g[k];
+    // B = r (D + D^T), r = -eps^2 / (2 h^alpha cos(alpha pi / 2)) > 0:
+    // b_0 = 2 r omega_1, b_1 = r (omega_0 + omega_2), b_k = r omega_{k+1} (k >= 2).
+    const double r = -eps * eps / (2.0 * std::pow(h, alpha) * std::cos(alpha * M_PI / 2.0));
+    T->bcol.assign(n, 0.0);
+    T->bcol[0] = 2.0 * r * w[1];
+    if (n > 1) T->bcol[1] = r * (w[0] + w[2]);
+    for (int k = 2; k < n; ++k) T->bcol[k] = r * w[k + 1];
+    // B is symmetric, b_{-k} = b_k, so b_{k-m+1} = b_{-(n-k)} = b_{n-k} with n = m-1:
+    // c_k = (b_k + b_{n-k}) / 2, s_k = (b_k - b_{n-k}) / 2 (k >= 1), c_0 = s_0 = b_0 / 2.
+    T->cfirst.assign(n, 0.0);
+    T->sfirst.assign(n, 0.0);
+    T->cfirst[0] = 0.5 * T->bcol[0];
+    T->sfirst[0] = 0.5 * T->bcol[0];
+    for (int k = 1; k < n; ++k) {
+        T->cfirst[k] = 0.5 * (T->bcol[k] + T->bcol[n - k]);
+        T->sfirst[k] = 0.5 * (T->bcol[k] - T->bcol[n - k]);
+    }
+    // cos / sin of pi m / n for m in [0, 2n)
+    std::vector<double> cs(2 * n), sn(2 * n);
+    for (int m = 0; m < 2 * n; ++m) sincospi_frac(m, n, &cs[m], &sn[m]);
+    // lambda_j = sum_k c_k e^{-2 pi i jk/n}; mu_j = sum_k s_k e^{i pi k/n} e^{-2 pi i jk/n}
+    //         = sum_k s_k e^{-i pi k (2j-1)/n}. Both are real because C and S are
+    // symmetric (c_k = c_{n-k}, s_{-k} = -s_{n-k}); the real parts are summed.
+    T->lambda.assign(n, 0.0);
+    T->mu.assign(n, 0.0);
+    const long long two_n = 2LL * n;
+    for (int j = 0; j < n; ++j) {
+        KahanSum sl, sm;
+        for (int k = 0; k < n; ++k) {
+            const long long ml = (2LL * j * k) % two_n;
+            long long mm = ((long long)k * (2LL * j - 1)) % two_n;
+            if (mm < 0) mm += two_n;
+            sl.add(T->cfirst[k] * cs[ml]);
+            sm.add(T->sfirst[k] * cs[mm]);
+        }
+        T->lambda[j] = sl.value();
+        T->mu[j] = sm.value();
+    }
+    // Factors with the inverse-FFT normalisation 1/n folded in.
+    T->eC.resize(n);
+    T->eS.resize(n);
+    for (int j = 0; j < n; ++j) {
+        T->eC[j] = std::exp(0.5 * tau * T->lambda[j]) / (double)n;
+        T->eS[j] = std::exp(tau * T->mu[j]) / (double)n;
+    }
+    // Twist e^{i pi k/n} and FFT twiddles e^{-2 pi i m/n}.
+    T->twist.resize(2 * n);
+    T->twid.resize(2 * n);
+    for (int k = 0; k < n; ++k) {
+        T->twist[2 * k] = cs[k];
+        T->twist[2 * k + 1] = sn[k];
+        T->twid[2 * k] = cs[(2 * k) % (2 * n)];
+        T->twid[2 * k + 1] = -sn[(2 * k) % (2 * n)];
+    }
+}
+
+sfac_status validate(const sfac_params* p, bool need_supported) {
+    if (!p) return fail(SFAC_EINVAL, "params is NULL");
+    if (p->dim < 1 || p->dim > 3) return fail(SFAC_EINVAL, "dim must be 1, 2 or 3");
+    if (p->reserved != 0) return fail(SFAC_EINVAL, "reserved field must be 0");
+    if (p->prec != SFAC_FP64 && p->prec != SFAC_FP32) return fail(SFAC_EINVAL, "prec must be SFAC_FP64 or SFAC_FP32");
+    if (!(std::isfinite(p->eps) && p->eps > 0)) return fail(SFAC_EINVAL, "eps must be finite and > 0");
+    if (!(std::isfinite(p->tau) && p->tau > 0)) return fail(SFAC_EINVAL, "tau must be finite and > 0");
+    if (!(std::isfinite(p->a) && std::isfinite(p->b) && p->b > p->a)) return fail(SFAC_EINVAL, "need finite a < b");
+    long long pts = 1;
+    for (int l = 0; l < p->dim; ++l) {
+        if (p->n[l] < 1) return fail(SFAC_EINVAL, "n[l] must be >= 1");
+        if (!(p->alpha[l] > 1.0 && p->alpha[l] < 2.0)) return fail(SFAC_EINVAL, "alpha[l] must lie in (1, 2)");
+        if (need_supported && (!is_pow2(p->n[l]) || p->n[l] < 4 || p->n[l] > 4096))
+            return fail(SFAC_EUNSUPPORTED, "n[l] must be a power of two in [4, 4096]");
+        pts *= p->n[l];
+    }
+    if (pts > (1LL << 34)) return fail(SFAC_EUNSUPPORTED, "grid too large");
+    return SFAC_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct sfac_plan {
+    sfac_params p;
+    int device = 0;
+    long long npts = 0;
+    void* dev_tables = nullptr;
+    struct Ax {
+        const void* eC;
+        const void* eS;
+        const void* twist;
+        const void* twid;
+    } ax[3] = {};
+    double jq_half_E = 0, jq_half_1mE = 0, jq_full_E = 0, jq_full_1mE = 0;
+    void* staging = nullptr;
+};
+
+namespace {
+
+size_t real_size(const sfac_plan* P) { return P->p.prec == SFAC_FP64 ? sizeof(double) : sizeof(float); }
+
+// Scoped switch to the plan's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+sfac_status launch_axis(sfac_plan* P, void* u, int ax, int jq_in, int jq_out, cudaStream_t st) {
+    long long inner = 1;
+    for (int l = 0; l < ax; ++l) inner *= P->p.n[l];
+    const int N = P->p.n[ax];
+    sfac::PassArgs a;
+    a.u = u;
+    a.inner = inner;
+    a.outer = P->npts / ((long long)N * inner);
+    a.clines = (ax == 0) ? (a.outer + 1) / 2 : a.outer * (inner / 2);
+    a.eC = P->ax[ax].eC;
+    a.eS = P->ax[ax].eS;
+    a.twist = P->ax[ax].twist;
+    a.twid = P->ax[ax].twid;
+    a.jq_in = jq_in != 0;
+    a.jq_in_E = jq_in == 2 ? P->jq_full_E : P->jq_half_E;
+    a.jq_in_1mE = jq_in == 2 ? P->jq_full_1mE : P->jq_half_1mE;
+    a.jq_out = jq_out != 0;
+    a.jq_out_E = jq_out == 2 ? P->jq_full_E : P->jq_half_E;
+    a.jq_out_1mE = jq_out == 2 ? P->jq_full_1mE : P->jq_half_1mE;
+    const cudaError_t err = (P->p.prec == SFAC_FP64) ? sfac::launch_pass_f64(N, a, st)
+                                                     : sfac::launch_pass_f32(N, a, st);
+    if (err != cudaSuccess) return cuda_fail(err, "axis pass launch");
+    return SFAC_OK;
+}
+
+sfac_status run_steps(sfac_plan* P, void* u, long long nsteps, cudaStream_t st) {
+    const int d = P->p.dim;
+    for (long long s = 0; s < nsteps; ++s) {
+        // J^Q_{tau/2} opens the first step and closes the last one; between two
+        // steps of one call the closing and opening halves act as one J^Q_{tau}.
+        const bool last = (s == nsteps - 1);
+        for (int ax = 0; ax < d; ++ax) {
+            const int jin = (ax == 0 && s == 0) ? 1 : 0;
+            const int jout = (ax == d - 1) ? (last ? 1 : 2) : 0;
+            const sfac_status r = launch_axis(P, u, ax, jin, jout, st);
+            if (r != SFAC_OK) return r;
+        }
+    }
+    return SFAC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfac_version(void) { return 100; }
+
+const char* sfac_last_error(void) { return g_last_error.c_str(); }
+
+sfac_status sfac_plan_tables(const sfac_params* params, int axis, double* lambda, double* mu,
+                             double* bcol, double* jq) {
+    sfac_status st = validate(params, false);
+    if (st != SFAC_OK) return st;
+    if (axis < 0 || axis >= params->dim) return fail(SFAC_EINVAL, "axis out of range");
+    AxisHost T;
+    try {
+        compute_axis(params->alpha[axis], params->eps, params->tau, params->a, params->b, params->n[axis], &T);
+    } catch (const std::bad_alloc&) {
+        return fail(SFAC_ENOMEM, "host allocation failed");
+    }
+    const int n = params->n[axis];
+    if (lambda) std::memcpy(lambda, T.lambda.data(), sizeof(double) * n);
+    if (mu) std::memcpy(mu, T.mu.data(), sizeof(double) * n);
+    if (bcol) std::memcpy(bcol, T.bcol.data(), sizeof(double) * n);
+    if (jq) {
+        jq[0] = std::exp(-params->tau);
+        jq[1] = -std::expm1(-params->tau);
+        jq[2] = std::exp(-2.0 * params->tau);
+        jq[3] = -std::expm1(-2.0 * params->tau);
+    }
+    return SFAC_OK;
+}
+
+sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan** out) {
+    if (!out) return fail(SFAC_EINVAL, "out is NULL");
+    *out = nullptr;
+    sfac_status st = validate(params, true);
+    if (st != SFAC_OK) return st;
+    sfac_plan* P = new (std::nothrow) sfac_plan();
+    if (!P) return fail(SFAC_ENOMEM, "host allocation failed");
+    P->p = *params;
+    for (int l = params->dim; l < 3; ++l) P->p.n[l] = 1;
+    P->npts = 1;
+    for (int l = 0; l < params->dim; ++l) P->npts *= params->n[l];
+    P->jq_half_E = std::exp(-params->tau);
+    P->jq_half_1mE = -std::expm1(-params->tau);
+    P->jq_full_E = std::exp(-2.0 * params->tau);
+    P->jq_full_1mE = -std::expm1(-2.0 * params->tau);
+
+    AxisHost host[3];
+    try {
+        for (int l = 0; l < params->dim; ++l)
+            compute_axis(params->alpha[l], params->eps, params->tau, params->a, params->b, params->n[l], &host[l]);
+    } catch (const std::bad_alloc&) {
+        delete P;
+        return fail(SFAC_ENOMEM, "host allocation failed");
+    }
+    cudaError_t err = cudaGetDevice(&P->device);
+    if (err != cudaSuccess) {
+        delete P;
+        return cuda_fail(err, "cudaGetDevice");
+    }
+    // One device block: per axis eC[n], eS[n], twist[2n], twid[2n] reals.
+    const size_t rs = real_size(P);
+    size_t off[3][4], total = 0;
+    for (int l = 0; l < params->dim; ++l) {
+        const size_t n = (size_t)params->n[l];
+        const size_t sz[4] = {n * rs, n * rs, 2 * n * rs, 2 * n * rs};
+        for (int q = 0; q < 4; ++q) {
+            off[l][q] = total;
+            total += align256(sz[q]);
+        }
+    }
+    std::vector<unsigned char> blob;
+    try {
+        blob.assign(total, 0);
+    } catch (const std::bad_alloc&) {
+        delete P;
+        return fail(SFAC_ENOMEM, "host allocation failed");
+    }
+    for (int l = 0; l < params->dim; ++l) {
+        const std::vector<double>* src[4] = {&host[l].eC, &host[l].eS, &host[l].twist, &host[l].twid};
+        for (int q = 0; q < 4; ++q) {
+            unsigned char* dst = blob.data() + off[l][q];
+            const std::vector<double>& v = *src[q];
+            if (rs == sizeof(double)) {
+                std::memcpy(dst, v.data(), v.size() * sizeof(double));
+            } else {
+                float* f = reinterpret_cast<float*>(dst);
+                for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];  // rounded once
+            }
+        }
+    }
+    err = cudaMalloc(&P->dev_tables, total);
+    if (err != cudaSuccess) {
+        delete P;
+        cudaGetLastError();
+        return fail(SFAC_ENOMEM, std::string("cudaMalloc of tables: ") + cudaGetErrorString(err));
+    }
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    err = cudaMemcpyAsync(P->dev_tables, blob.data(), total, cudaMemcpyHostToDevice, st_);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st_);
+    if (err != cudaSuccess) {
+        cudaFree(P->dev_tables);
+        delete P;
+        return cuda_fail(err, "table upload");
+    }
+    unsigned char* base = static_cast<unsigned char*>(P->dev_tables);
+    for (int l = 0; l < params->dim; ++l) {
+        P->ax[l].eC = base + off[l][0];
+        P->ax[l].eS = base + off[l][1];
+        P->ax[l].twist = base + off[l][2];
+        P->ax[l].twid = base + off[l][3];
+    }
+    *out = P;
+    return SFAC_OK;
+}
+
+sfac_status sfac_plan_destroy(sfac_plan* plan) {
+    if (!plan) return SFAC_OK;
+    sfac_status st = SFAC_OK;
+    {
+        DeviceGuard g(plan->device);
+        cudaError_t err = cudaDeviceSynchronize();
+        if (err != cudaSuccess) st = cuda_fail(err, "synchronise before destroy");
+        if (plan->dev_tables) cudaFree(plan->dev_tables);
+        if (plan->staging) cudaFree(plan->staging);
+    }
+    delete plan;
+    return st;
+}
+
+sfac_status sfac_step(sfac_plan* plan, void* u_dev, long long nsteps, void* stream) {
+    if (!plan) return fail(SFAC_EINVAL, "plan is NULL");
+    if (!u_dev) return fail(SFAC_EINVAL, "u_dev is NULL");
+    if (nsteps < 0) return fail(SFAC_EINVAL, "nsteps must be >= 0");
+    if (reinterpret_cast<uintptr_t>(u_dev) % 16 != 0) return fail(SFAC_EINVAL, "u_dev must be 16-byte aligned");
+    if (nsteps == 0) return SFAC_OK;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
+    return run_steps(plan, u_dev, nsteps, static_cast<cudaStream_t>(stream));
+}
+
+sfac_status sfac_axis_pass(sfac_plan* plan, void* u_dev, int axis, int jq_in, int jq_out, void* stream) {
+    if (!plan) return fail(SFAC_EINVAL, "plan is NULL");
+    if (!u_dev) return fail(SFAC_EINVAL, "u_dev is NULL");
+    if (axis < 0 || axis >= plan->p.dim) return fail(SFAC_EINVAL, "axis out of range");
+    if (jq_in < 0 || jq_in > 2 || jq_out < 0 || jq_out > 2) return fail(SFAC_EINVAL, "jq mode must be 0, 1 or 2");
+    if (reinterpret_cast<uintptr_t>(u_dev) % 16 != 0) return fail(SFAC_EINVAL, "u_dev must be 16-byte aligned");
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
+    return launch_axis(plan, u_dev, axis, jq_in, jq_out, static_cast<cudaStream_t>(stream));
+}
+
+sfac_status sfac_solve(sfac_plan* plan, void* u_dev, double T, void* stream) {
+    if (!plan) return fail(SFAC_EINVAL, "plan is NULL");
+    if (!(std::isfinite(T) && T >= 0)) return fail(SFAC_EINVAL, "T must be finite and >= 0");
+    const double q = T / plan->p.tau;
+    const double r = std::nearbyint(q);
+    if (std::fabs(q - r) > 1e-9 * std::fmax(1.0, q)) return fail(SFAC_EINVAL, "T is not a whole number of steps");
+    return sfac_step(plan, u_dev, (long long)r, stream);
+}
+
+sfac_status sfac_step_host(sfac_plan* plan, void* u_host, long long nsteps, void* stream) {
+    if (!plan) return fail(SFAC_EINVAL, "plan is NULL");
+    if (!u_host) return fail(SFAC_EINVAL, "u_host is NULL");
+    if (nsteps < 0) return fail(SFAC_EINVAL, "nsteps must be >= 0");
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
+    const size_t bytes = (size_t)plan->npts * real_size(plan);
+    cudaError_t err;
+    if (!plan->staging) {
+        err = cudaMalloc(&plan->staging, bytes);
+        if (err != cudaSuccess) {
+            plan->staging = nullptr;
+            cudaGetLastError();
+            return fail(SFAC_ENOMEM, std::string("cudaMalloc of staging buffer: ") + cudaGetErrorString(err));
+        }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    err = cudaMemcpyAsync(plan->staging, u_host, bytes, cudaMemcpyHostToDevice, st);
+    if (err != cudaSuccess) return cuda_fail(err, "host-to-device copy");
+    sfac_status s = run_steps(plan, plan->staging, nsteps, st);
+    if (s != SFAC_OK) return s;
+    err = cudaMemcpyAsync(u_host, plan->staging, bytes, cudaMemcpyDeviceToHost, st);
+    if (err != cudaSuccess) return cuda_fail(err, "device-to-host copy");
+    err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return cuda_fail(err, "stream synchronise");
+    return SFAC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle on
+the same seeded inputs. FP64 bar: relative max-norm error <= 1e-12."""
+import numpy as np
+import pytest
+
+import paper_2209_08437_gb300 as S
+import sfac_inputs as I
+from oracle import sfac_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def rel_err(got, ref):
+    return float(np.abs(got - ref).max() / np.abs(ref).max())
+
+
+def to_dev(u0, prec):
+    dt = torch.float64 if prec == S.SFAC_FP64 else torch.float32
+    return torch.tensor(np.ascontiguousarray(u0), dtype=dt, device="cuda")
+
+
+def gpu_run(prob, u0, nsteps, prec=S.SFAC_FP64):
+    with S.Plan.for_problem(prob, prec) as plan:
+        u = to_dev(u0, prec)
+        plan.step(u, nsteps)
+        torch.cuda.synchronize()
+        return u.double().cpu().numpy()
+
+
+SHAPES_2D = [(4, 4), (4, 8), (8, 4), (16, 16), (64, 32), (32, 128), (256, 256), (1024, 8),
+             (8, 1024), (2048, 4), (4, 4096)]
+SHAPES_3D = [(4, 4, 4), (4, 8, 16), (32, 4, 8), (16, 16, 16), (64, 8, 32)]
+
+
+@pytest.mark.parametrize("n", SHAPES_2D + SHAPES_3D + [(16,), (1024,)], ids=str)
+def test_axis_pass_equals_dense_factor(n):
+    """One fused pass (no J^Q) along each axis equals the oracle's dense
+    P = e^{tau/2 C} e^{tau S} e^{tau/2 C} applied to every line of that axis."""
+    prob = I.Problem(n=n, alpha=(1.3, 1.7, 1.5)[: len(n)], eps=0.1, tau=0.02)
+    u0 = I.random_field(prob, 3, -1.0, 1.0)
+    sch = O.Scheme.for_problem(prob)
+    with S.Plan.for_problem(prob) as plan:
+        for ax in range(len(n)):
+            u = to_dev(u0, S.SFAC_FP64)
+            plan.axis_pass(u, ax, 0, 0)
+            torch.cuda.synchronize()
+            ref = O.apply_axis(u0, sch.P[ax], ax + 1)
+            assert rel_err(u.cpu().numpy(), ref) <= TOL64, (n, ax)
+
+
+@pytest.mark.parametrize("jin,jout", [(1, 0), (0, 1), (2, 0), (0, 2), (1, 2)])
+def test_axis_pass_nonlinear_modes(jin, jout):
+    prob = I.Problem(n=(32, 16), alpha=(1.4, 1.6), eps=0.1, tau=0.05)
+    u0 = I.random_field(prob, 4, -1.0, 1.0)
+    sch = O.Scheme.for_problem(prob)
+    s = {0: None, 1: 0.5 * prob.tau, 2: prob.tau}
+    with S.Plan.for_problem(prob) as plan:
+        u = to_dev(u0, S.SFAC_FP64)
+        plan.axis_pass(u, 1, jin, jout)
+        torch.cuda.synchronize()
+    ref = u0 if s[jin] is None else O.nonlinear_flow(u0, s[jin])
+    ref = O.apply_axis(ref, sch.P[1], 2)
+    ref = ref if s[jout] is None else O.nonlinear_flow(ref, s[jout])
+    assert rel_err(u.cpu().numpy(), ref) <= TOL64
+
+
+@pytest.mark.parametrize("n", SHAPES_2D[:8] + SHAPES_3D + [(64,)], ids=str)
+@pytest.mark.parametrize("nsteps", [1, 3, 10])
+def test_steps_match_oracle(n, nsteps):
+    prob = I.Problem(n=n, alpha=(1.2, 1.8, 1.5)[: len(n)], eps=0.08, tau=0.01)
+    u0 = I.random_field(prob, 5)
+    ref = O.Scheme.for_problem(prob).run(u0, nsteps)
+    assert rel_err(gpu_run(prob, u0, nsteps), ref) <= TOL64
+
+
+def test_config1_full_run():
+    """2D n=64, alpha=(1.5,1.5), eps=0.1, tau=0.01, 100 steps, u0 ~ U[-0.9,0.9] seed 0."""
+    prob = I.CONFIG1
+    u0 = I.config1_u0()
+    ref = O.solve(prob, u0)
+    assert rel_err(gpu_run(prob, u0, prob.steps), ref) <= TOL64
+
+
+def test_config2_full_run():
+    """2D n=1024, alpha=(1.3,1.7), eps=0.05, tau=1e-3, the full 1000 steps, against
+    the oracle's spectral route (its dense route alone drifts by ~3e-12 over 1000
+    steps from its own rounding; the spectral route stays within ~1e-15 per step)."""
+    prob = I.CONFIG2
+    u0 = I.config2_u0()
+    ref = O.solve(prob, u0, route="spectral")
+    err = rel_err(gpu_run(prob, u0, prob.steps), ref)
+    print(f"config2 FP64 rel err vs spectral oracle {err:.3e}")
+    assert err <= TOL64
+
+
+def test_config2_first_100_steps_dense():
+    prob = I.CONFIG2
+    u0 = I.config2_u0()
+    ref = O.solve(prob, u0, 100)
+    err = rel_err(gpu_run(prob, u0, 100), ref)
+    print(f"config2 100 steps FP64 rel err vs dense oracle {err:.3e}")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("n,alpha,seed", [(256, 1.7, 21), (1024, 1.3, 22)])
+def test_axis_pass_against_30_digit_reference(n, alpha, seed):
+    """One FP64 pass (1D, no J^Q) against stored 30-digit values of the factor."""
+    from tests.conftest import read_golden
+    y = np.array([float(r[0]) for r in read_golden(f"mp_axis_factor_n{n}.txt")])
+    x = I.uniform(seed, n, -1.0, 1.0)
+    prob = I.Problem(n=(n,), alpha=(alpha,), eps=0.05, tau=1e-3)
+    with S.Plan.for_problem(prob) as plan:
+        u = to_dev(x, S.SFAC_FP64)
+        plan.axis_pass(u, 0, 0, 0)
+        torch.cuda.synchronize()
+    err = float(np.abs(u.cpu().numpy() - y).max())
+    print(f"n={n}: GPU pass vs 30-digit reference {err:.3e}")
+    assert err <= 5e-15
+
+
+def test_config3_first_20_steps():
+    """3D n=256^3, alpha=(1.2,1.5,1.8), eps=0.08, tau=2e-3: the first 20 steps
+    (the dense oracle costs 3 * 256^4 FMA per step)."""
+    prob = I.CONFIG3
+    u0 = I.config3_u0()
+    ref = O.solve(prob, u0, 20)
+    err = rel_err(gpu_run(prob, u0, 20), ref)
+    print(f"config3 FP64 rel err {err:.3e}")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("dims,n", [(2, 32), (3, 16), (1, 256)])
+def test_maximum_principle_on_gpu(dims, n):
+    """Theorem 1 on the device path: max|u| stays <= 1 for any tau when |u0| <= 1."""
+    for tau in (1e-3, 0.1, 10.0):
+        prob = I.Problem(n=(n,) * dims, alpha=(1.9, 1.1, 1.6)[:dims], eps=0.3, tau=tau)
+        u = to_dev(I.random_field(prob, 12, -1.0, 1.0), S.SFAC_FP64)
+        with S.Plan.for_problem(prob) as plan:
+            for _ in range(10):
+                plan.step(u, 1)
+                assert float(u.abs().max()) <= 1 + 1e-14
+
+
+def test_merged_half_flows_and_call_boundaries():
+    """step(k) merges inner half flows into J^Q_tau; k calls of step(1) do not.
+    Both are the same scheme: equal to rounding."""
+    prob = I.Problem(n=(64, 64), alpha=(1.3, 1.6), eps=0.1, tau=0.05)
+    u0 = I.random_field(prob, 6)
+    with S.Plan.for_problem(prob) as plan:
+        a = to_dev(u0, S.SFAC_FP64)
+        b = to_dev(u0, S.SFAC_FP64)
+        plan.step(a, 7)
+        for _ in range(7):
+            plan.step(b, 1)
+        torch.cuda.synchronize()
+    assert rel_err(a.cpu().numpy(), b.cpu().numpy()) <= 1e-14
+
+
+def test_pass_sequence_is_one_step_bitwise():
+    prob = I.Problem(n=(32, 16, 8), alpha=(1.3, 1.6, 1.2), eps=0.1, tau=0.05)
+    u0 = I.random_field(prob, 7)
+    with S.Plan.for_problem(prob) as plan:
+        a = to_dev(u0, S.SFAC_FP64)
+        b = to_dev(u0, S.SFAC_FP64)
+        plan.step(a, 1)
+        plan.axis_pass(b, 0, 1, 0)
+        plan.axis_pass(b, 1, 0, 0)
+        plan.axis_pass(b, 2, 0, 1)
+        torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_solve_zero_steps_and_host_path():
+    prob = I.Problem(n=(64, 128), alpha=(1.3, 1.6), eps=0.1, tau=0.01)
+    u0 = I.random_field(prob, 8)
+    with S.Plan.for_problem(prob) as plan:
+        a = to_dev(u0, S.SFAC_FP64)
+        plan.step(a, 0)
+        torch.cuda.synchronize()
+        assert np.array_equal(a.cpu().numpy(), u0)
+        plan.solve(a, 0.05)          # 5 steps
+        b = to_dev(u0, S.SFAC_FP64)
+        plan.step(b, 5)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        with pytest.raises(S.SfacError):
+            plan.solve(a, 0.055)      # not a whole number of steps
+        h = np.array(u0, copy=True)
+        plan.step_host(h, 5)
+        assert np.array_equal(h, b.cpu().numpy())
+
+
+@pytest.mark.parametrize("which", ["config1", "config2_100", "config3_10"])
+def test_fp32_error_against_fp64_oracle(which):
+    """FP32 passes with FP64-computed tables: max-norm error against the FP64
+    oracle stays below 1e-5."""
+    if which == "config1":
+        prob, u0, k = I.CONFIG1, I.config1_u0(), I.CONFIG1.steps
+    elif which == "config2_100":
+        prob, u0, k = I.CONFIG2, I.config2_u0(), 100
+    else:
+        prob, u0, k = I.CONFIG3, I.config3_u0(), 10
+    ref = O.solve(prob, u0, k)
+    u32 = np.asarray(u0, dtype=np.float32).astype(np.float64)
+    got = gpu_run(prob, u32, k, S.SFAC_FP32)
+    err = float(np.abs(got - ref).max())
+    print(f"{which}: FP32 max-norm error {err:.3e}")
+    assert err <= 1e-5

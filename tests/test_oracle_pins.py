@@ -98,6 +98,7 @@ def test_alpha2_reduces_to_laplacian_and_expm():
     lam, V = laplacian_spectrum(n, eps, h)
     tau = 0.37
     closed = (V * np.exp(tau * lam)) @ V.T
+    np.testing.assert_allclose(O.expm_dense(B, tau), closed, atol=1e-13)
     np.testing.assert_allclose(O.expm_symmetric(B, tau), closed, atol=1e-13)
 
 
@@ -152,11 +153,12 @@ def test_expm_against_pade_and_contractivity(alpha, n):
     eps, h, tau = 0.1, 2.0 / (n + 1), 0.05
     C, S = O.split_CS(O.matrix_B(alpha, eps, h, n))
     for M, t in ((C, tau / 2), (S, tau), (C + S, tau)):
-        E = O.expm_symmetric(M, t)
-        np.testing.assert_allclose(E, scipy.linalg.expm(t * M), atol=1e-13, rtol=1e-12)
+        E = O.expm_dense(M, t)
+        # scaling-and-squaring against the eigendecomposition route
+        np.testing.assert_allclose(E, O.expm_symmetric(M, t), atol=1e-13, rtol=1e-12)
     for M in (C, S):  # Lemmas 1-2: ||e^{tM}||_inf <= 1
         for t in (1e-3, 0.1, 10.0):
-            assert np.abs(O.expm_symmetric(M, t)).sum(axis=1).max() <= 1 + 1e-12
+            assert np.abs(O.expm_dense(M, t)).sum(axis=1).max() <= 1 + 1e-12
 
 
 @pytest.mark.parametrize("alpha,n", [(1.3, 8), (1.7, 13), (1.45, 32)])
@@ -167,6 +169,44 @@ def test_two_level_factor_by_dft(alpha, n):
     Q = O.axis_factor_by_dft(alpha, eps, h, n, tau)
     np.testing.assert_allclose(P, Q, atol=1e-13)
     np.testing.assert_allclose(P, P.T, atol=1e-14)  # symmetric: a product E_C E_S E_C
+
+
+def test_mp_yardstick_equals_dense_definition():
+    """The 30-digit evaluation (Toeplitz columns from the Remark-1 spectra) against the
+    dense definition e^{tau/2 C} e^{tau S} e^{tau/2 C} on small n."""
+    from oracle.sfac_oracle_mp import mp_axis_apply_f64
+    for n, alpha in ((5, 1.3), (8, 1.8), (16, 1.5)):
+        h, tau = 2.0 / (n + 1), 0.3
+        x = I.uniform(40 + n, n, -1, 1)
+        P = O.axis_two_level_factor(alpha, 0.2, h, n, tau)
+        np.testing.assert_allclose(mp_axis_apply_f64(alpha, 0.2, h, n, tau, x), P @ x, atol=2e-15)
+
+
+def _mp_golden(n):
+    rows = read_golden(f"mp_axis_factor_n{n}.txt")
+    return np.array([float(r[0]) for r in rows])
+
+
+@pytest.mark.parametrize("n,alpha,seed,tol_dense", [(256, 1.7, 21, 5e-15), (1024, 1.3, 22, 1e-14)])
+def test_routes_against_30_digit_reference(n, alpha, seed, tol_dense):
+    """Both FP64 routes of the oracle against the stored 30-digit values: the dense
+    route within its rounding (a few 1e-15), the spectral route within 3e-15."""
+    x = I.uniform(seed, n, -1.0, 1.0)
+    y = _mp_golden(n)
+    h = 2.0 / (n + 1)
+    P = O.axis_two_level_factor(alpha, 0.05, h, n, 1e-3)
+    assert np.abs(P @ x - y).max() <= tol_dense
+    sf = O.SpectralFactor(alpha, 0.05, h, n, 1e-3)
+    assert np.abs(sf.apply(x, 1) - y).max() <= 3e-15
+
+
+@pytest.mark.parametrize("n", [(16,), (32, 8), (8, 16, 4)], ids=str)
+def test_dense_and_spectral_routes_agree(n):
+    prob = I.Problem(n=n, alpha=(1.25, 1.75, 1.5)[: len(n)], eps=0.1, tau=0.02)
+    u0 = I.random_field(prob, 9)
+    a = O.solve(prob, u0, 5)
+    b = O.solve(prob, u0, 5, route="spectral")
+    assert np.abs(a - b).max() <= 1e-13
 
 
 def test_circulant_B_makes_second_level_exact():
