@@ -33,6 +33,8 @@
 #ifndef SFAC_H
 #define SFAC_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -127,6 +129,123 @@ sfac_status sfac_step_host(sfac_plan* plan, void* u_host, long long nsteps, void
  * 1 - e^{-2 tau}}, the constants of J^Q_{tau/2} and J^Q_{tau} (eq. (nonlinear_operator)). */
 sfac_status sfac_plan_tables(const sfac_params* params, int axis, double* lambda, double* mu,
                              double* bcol, double* jq);
+
+/* ------------------------------------------------------------------------ */
+/* Batched runner: many independent problems in one persistent launch.       */
+/* ------------------------------------------------------------------------ */
+
+/* A batch of `count` independent problems, each advanced by eq. (finalstrang)
+ * with its own grid, alpha, eps, tau and step count. One persistent kernel
+ * runs every instance: its work items (groups of lines of one axis pass of one
+ * instance at one step) are claimed by warps in an order that respects each
+ * instance's pass order; a warp starts an item once every item of the same
+ * instance's previous pass has finished (per-instance completion counters).
+ * The batch owns its tables, schedule and scratch counters; the caller owns
+ * the fields. */
+typedef struct sfac_batch sfac_batch;
+
+/* Build a batch: params[i] describes instance i (dim 2 or 3; every n[l] a power
+ * of two in [32, 512]; one precision for all). FP64 tables per instance and
+ * axis are computed on the host (as in sfac_plan_create) and uploaded once on
+ * `stream` (synchronised). SFAC_EUNSUPPORTED for other shapes. */
+sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream, sfac_batch** out);
+
+/* Release the batch (synchronises the device first). NULL is a no-op. */
+sfac_status sfac_batch_destroy(sfac_batch* batch);
+
+/* Bind fields and step counts: u_dev[i] is instance i's device field (layout of
+ * sfac_step, 16-byte aligned), nsteps[i] >= 0 its number of steps. Builds the
+ * phase schedule on the host and uploads it (synchronises `stream`). */
+sfac_status sfac_batch_prepare(sfac_batch* batch, void* const* u_dev, const long long* nsteps, void* stream);
+
+/* Enqueue the prepared run on `stream`: reset the scratch counters, launch the
+ * persistent kernel, copy its status flag to host memory. Asynchronous, with no
+ * host synchronisation and no allocation, so it can be captured in a CUDA
+ * graph and replayed (each replay advances every field again). */
+sfac_status sfac_batch_launch(sfac_batch* batch, void* stream);
+
+/* Synchronise `stream` and report the status of the last launch: SFAC_ETIMEOUT
+ * if a dependency wait gave up (the kernel then returns early and fields may be
+ * partly advanced), SFAC_ECUDA for a CUDA error. */
+sfac_status sfac_batch_wait(sfac_batch* batch, void* stream);
+
+/* prepare + launch + wait. */
+sfac_status sfac_batch_step(sfac_batch* batch, void* const* u_dev, const long long* nsteps, void* stream);
+
+/* Autotuner: time every kernel shape (warps per CTA, values per thread, i.e. the
+ * radix schedule of lines up to 256 points, and line groups per work item) on
+ * copies of the prepared fields for min(nsteps, max_steps) steps, keep the
+ * fastest and re-prepare. Requires a prepared batch; the fields are not
+ * changed. *choice (may be NULL) receives the chosen shape's index. */
+sfac_status sfac_batch_autotune(sfac_batch* batch, int max_steps, void* stream, int* choice);
+
+/* Select a kernel shape by index in [0, sfac_batch_num_configs()) (takes effect
+ * at the next prepare) and read back the current one. */
+sfac_status sfac_batch_set_config(sfac_batch* batch, int config);
+sfac_status sfac_batch_get_config(const sfac_batch* batch, int* config, int* warps_per_cta,
+                                  int* values_per_thread, int* groups_per_item);
+int sfac_batch_num_configs(void);
+
+/* Failure-detection controls: every dependency wait polls at most spin_limit
+ * times (about 100 ns apart) before the launch gives up with SFAC_ETIMEOUT.
+ * hold_instance >= 0 makes that instance's second pass wait for a completion
+ * count that is never reached, to exercise the bounded wait (-1: off). Takes
+ * effect at the next prepare. */
+sfac_status sfac_batch_set_wait_limit(sfac_batch* batch, long long spin_limit, int hold_instance);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of requests of different sizes.              */
+/* ------------------------------------------------------------------------ */
+
+/* A server owns one device arena of `arena_bytes`. An admitted request gets a
+ * slot whose field and per-axis tables (as in sfac_plan_create) stay resident in
+ * the arena until its result is fetched. A round advances every active slot by
+ * up to `chunk` steps in one persistent launch of the batched kernel, so
+ * requests admitted while a round runs join the next round. A slot always
+ * advances in whole chunks counted from its own first step, so its result does
+ * not depend on which other requests share its rounds. */
+typedef struct sfac_server sfac_server;
+
+/* Create a server with `max_slots` slots for problems of precision `prec`.
+ * Allocates the arena, the scratch counters and an internal copy stream. */
+sfac_status sfac_server_create(size_t arena_bytes, int max_slots, int prec, void* stream, sfac_server** out);
+
+/* Release everything (synchronises the device first). NULL is a no-op. */
+sfac_status sfac_server_destroy(sfac_server* server);
+
+/* Arena bytes one request with these parameters occupies (field + tables). */
+sfac_status sfac_server_request_bytes(const sfac_params* params, size_t* bytes);
+
+/* Admit a request: dim 2 or 3, every n[l] a power of two in [32, 512], the
+ * server's precision; u0_host holds its initial field (layout of sfac_step);
+ * nsteps >= 0. Computes its FP64 tables on the host and copies field and tables
+ * into the arena on the internal copy stream (synchronised), which may overlap
+ * a round in flight. Returns SFAC_ENOMEM, and admits nothing, when no slot or
+ * no arena block is free: admission is by device memory, the caller keeps the
+ * request queued and retries after results are fetched. *slot receives the slot. */
+sfac_status sfac_server_admit(sfac_server* server, const sfac_params* params, const void* u0_host,
+                              long long nsteps, int* slot);
+
+/* Launch one round on `stream`: every slot with steps left advances by
+ * min(chunk, steps left) steps (kernel shape `shape`, an index as in
+ * sfac_batch_set_config). Asynchronous; at most one round in flight. */
+sfac_status sfac_server_round(sfac_server* server, long long chunk, int shape, void* stream);
+
+/* Wait for the round in flight (synchronises `stream`) and list the slots whose
+ * steps are all done: up to max_finished slot numbers go to finished[],
+ * *nfinished receives their count. SFAC_ETIMEOUT if a dependency wait gave up. */
+sfac_status sfac_server_wait(sfac_server* server, void* stream, int* finished, int max_finished,
+                             int* nfinished);
+
+/* Copy a slot's field to u_host (if not NULL; on the internal copy stream,
+ * synchronised, so it may overlap a round in flight that does not include the
+ * slot) and, if release != 0, free its slot and arena block. */
+sfac_status sfac_server_fetch(sfac_server* server, int slot, void* u_host, int release);
+
+/* Free arena bytes, largest free block, slots in use and slot capacity (each
+ * pointer may be NULL). */
+sfac_status sfac_server_info(const sfac_server* server, size_t* free_bytes, size_t* largest_free,
+                             int* active, int* capacity);
 
 /* Message describing the calling thread's most recent failure ("" if none). */
 const char* sfac_last_error(void);

@@ -1,0 +1,205 @@
+// sfac_batch.cuh - one persistent launch that advances many independent SFAC
+// problems of uneven sizes, orders and step counts.
+//
+// Work is cut into items: an item is `mult` warp-groups of lines of one
+// instance's axis pass at one step (a warp-group is the 32/T lines one warp
+// holds, see warp_pass_lines). Items are numbered phase by phase, a phase being
+// (step s, axis a) over every instance still active there, so the numbering is
+// a topological order of the dependencies: a pass may start once every item of
+// the same instance's previous pass has finished (the previous axis of the same
+// step, or the last axis of step s-1: eq. (finalstrang) applies the axes one
+// after another and J^Q between steps).
+//
+// Each warp claims the next item from a global counter, waits until the
+// instance's completion counter reaches the number of items of its earlier
+// passes, runs the fused pass on its lines and adds one to that counter. Items
+// are claimed in increasing order, so the item a warp waits on was claimed
+// earlier by a running warp: the scheme cannot deadlock. Every wait is bounded:
+// past `spin_limit` polls the warp records an error and leaves, and every other
+// warp leaves at its next poll.
+#pragma once
+
+#include "sfac_batch_launch.h"
+#include "sfac_pass.cuh"
+
+namespace sfac {
+
+// Shared memory per warp: the largest (32/T) * (N + N/E) over the supported
+// lengths, 544 complex values (32 <= N <= 512, E <= 16).
+constexpr int BATCH_REGION = 544;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// First index j in [lo, hi) with arr[j] > key (hi if none); arr ascending.
+// The 32 lanes probe evenly spaced positions each round.
+__device__ __forceinline__ long long warp_upper_bound(const long long* arr, long long lo, long long hi,
+                                                      long long key, int lane) {
+    while (hi - lo > 32) {
+        const long long step = (hi - lo + 31) / 32;
+        const long long idx = lo + lane * step;
+        const bool gt = idx < hi ? (__ldg(arr + idx) > key) : true;
+        const unsigned m = __ballot_sync(0xffffffffu, gt);
+        if (m == 0) {
+            lo = lo + 31 * step + 1;
+            continue;
+        }
+        const int f = __ffs(m) - 1;
+        const long long nhi = lo + f * step < hi ? lo + f * step : hi;
+        if (f > 0) lo = lo + (f - 1) * step + 1;
+        hi = nhi;
+    }
+    const long long idx = lo + lane;
+    const bool gt = idx < hi ? (__ldg(arr + idx) > key) : true;
+    const unsigned m = __ballot_sync(0xffffffffu, gt);
+    return m ? lo + (__ffs(m) - 1) : hi;
+}
+
+// Lines per warp-group for length N with ES values per thread below N = 512.
+template <int ES>
+__host__ __device__ constexpr int batch_elems(int N) {
+    return N >= 512 ? 16 : ES;
+}
+
+// One warp-group of lines; kept out of line so that each (R, N, E, axis kind)
+// body is compiled once and shared by the batch kernels.
+template <typename R, int N, int E, bool STRIDED>
+__device__ __noinline__ void batch_group(const PassArgs& pa, long long first, C2<R>* region, int lane) {
+    warp_pass_lines<R, N, E, STRIDED, true>(pa, first, region, lane);
+}
+
+template <typename R, int N, int E>
+__device__ __forceinline__ void batch_lines(const PassArgs& pa, bool strided, long long first, C2<R>* region,
+                                            int lane) {
+    if (strided) batch_group<R, N, E, true>(pa, first, region, lane);
+    else batch_group<R, N, E, false>(pa, first, region, lane);
+}
+
+// Launched with blockDim.x = 32 * (warps per CTA) <= 256 and
+// BATCH_REGION complex values of dynamic shared memory per warp.
+template <typename R, int ES>
+__global__ void __launch_bounds__(256)
+batch_kernel(const BatchSchedule b) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C2<R>* region = reinterpret_cast<C2<R>*>(smem_raw) + warp * BATCH_REGION;
+    int p = 0;  // phase of the last item: claimed items increase, so p only moves forward
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(b.counter, 1ULL);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if ((long long)item >= b.total_items) break;
+        while (__ldg(b.phase_base + p + 1) <= (long long)item) ++p;
+        const long long local = (long long)item - __ldg(b.phase_base + p);
+        const long long f0 = __ldg(b.phase_first + p), f1 = __ldg(b.phase_first + p + 1);
+        const long long slot = warp_upper_bound(b.slot_cum, f0, f1, local, lane);
+        const int ii = __ldg(b.slot_inst + slot);
+        const long long g = local - (slot > f0 ? __ldg(b.slot_cum + slot - 1) : 0);
+        const int s = __ldg(b.phase_step + p), a = __ldg(b.phase_axis + p);
+        const BatchInst& I = b.inst[ii];
+
+        // Wait for every item of this instance's earlier passes.
+        long long target = 0;
+        for (int l = 0; l < I.dim; ++l) target += (long long)I.items[l];
+        target *= s;
+        for (int l = 0; l < a; ++l) target += I.items[l];
+        if (ii == b.hold_instance && (s > 0 || a > 0)) target += 1;  // never satisfied
+        int ok = 1;
+        if (lane == 0) {
+            long long polls = 0;
+            while ((long long)ld_acquire_u64(b.done + ii) < target) {
+                if (ld_volatile_i32(b.error) != 0) { ok = 0; break; }
+                if (++polls > b.spin_limit) {
+                    atomicCAS(b.error, 0, SFAC_BATCH_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        __syncwarp();
+
+        // The pass this item belongs to.
+        const int N = I.n[a];
+        long long inner = 1;
+        for (int l = 0; l < a; ++l) inner *= I.n[l];
+        PassArgs pa;
+        pa.u = I.u;
+        pa.inner = inner;
+        pa.outer = I.npts / ((long long)N * inner);
+        pa.clines = (a == 0) ? (pa.outer + 1) / 2 : pa.outer * (inner / 2);
+        pa.eC = I.tab[a][0];
+        pa.eS = I.tab[a][1];
+        pa.twist = I.tab[a][2];
+        pa.twid = I.tab[a][3];
+        // J^Q_{tau/2} opens step 0 and closes the last step; inner steps merge
+        // the closing and opening halves into J^Q_tau.
+        pa.jq_in = (a == 0 && s == 0);
+        pa.jq_in_E = I.jq[0];
+        pa.jq_in_1mE = I.jq[1];
+        pa.jq_out = (a == I.dim - 1);
+        const bool last = (s == I.steps - 1);
+        pa.jq_out_E = last ? I.jq[0] : I.jq[2];
+        pa.jq_out_1mE = last ? I.jq[1] : I.jq[3];
+
+        const int lpw = 32 * batch_elems<ES>(N) / N;
+        const bool strided = a > 0;
+        for (int m = 0; m < b.mult; ++m) {
+            const long long first = (g * b.mult + m) * lpw;
+            if (first >= pa.clines) break;
+            switch (N) {
+                case 32: batch_lines<R, 32, ES>(pa, strided, first, region, lane); break;
+                case 64: batch_lines<R, 64, ES>(pa, strided, first, region, lane); break;
+                case 128: batch_lines<R, 128, ES>(pa, strided, first, region, lane); break;
+                case 256: batch_lines<R, 256, ES>(pa, strided, first, region, lane); break;
+                default: batch_lines<R, 512, 16>(pa, strided, first, region, lane); break;
+            }
+            __syncwarp();
+        }
+        // Publish: the stores above happen before the count is raised.
+        if (lane == 0) {
+            __threadfence();
+            atomicAdd(b.done + ii, 1ULL);
+        }
+    }
+}
+
+}  // namespace sfac
+
+namespace sfac {
+
+// Set the kernel's shared-memory limit and return its persistent grid (one CTA
+// per resident slot on every SM). Called when a run is prepared, outside any
+// stream capture.
+template <typename R, int ES>
+cudaError_t setup_batch(int wpb, int sms, int* grid) {
+    if (wpb < 1 || wpb > 8) return cudaErrorInvalidValue;
+    auto kern = batch_kernel<R, ES>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(8 * sizeof(C2<R>) * BATCH_REGION));
+    if (err != cudaSuccess) return err;
+    const size_t smem = sizeof(C2<R>) * (size_t)wpb * BATCH_REGION;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
+    if (err != cudaSuccess) return err;
+    *grid = (per_sm < 1 ? 1 : per_sm) * sms;
+    return cudaSuccess;
+}
+
+// Enqueue only (no attribute calls, no allocation): safe inside a graph capture.
+template <typename R, int ES>
+cudaError_t launch_batch(int wpb, int grid, const BatchSchedule& sc, cudaStream_t s) {
+    if (wpb < 1 || wpb > 8 || grid < 1) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(C2<R>) * (size_t)wpb * BATCH_REGION;
+    batch_kernel<R, ES><<<grid, wpb * 32, smem, s>>>(sc);
+    return cudaGetLastError();
+}
+
+}  // namespace sfac

@@ -1,0 +1,15 @@
+// FP32 batch kernels (values per thread 8 or 16 for lines up to 256 points).
+#include "sfac_batch.cuh"
+
+namespace sfac {
+cudaError_t setup_batch_f32(int wpb, int es, int sms, int* grid) {
+    if (es == 16) return setup_batch<float, 16>(wpb, sms, grid);
+    if (es == 8) return setup_batch<float, 8>(wpb, sms, grid);
+    return cudaErrorInvalidValue;
+}
+cudaError_t launch_batch_f32(int wpb, int es, int grid, const BatchSchedule& sc, cudaStream_t s) {
+    if (es == 16) return launch_batch<float, 16>(wpb, grid, sc, s);
+    if (es == 8) return launch_batch<float, 8>(wpb, grid, sc, s);
+    return cudaErrorInvalidValue;
+}
+}  // namespace sfac

@@ -1,0 +1,68 @@
+// sfac_batch_launch.h - host entry points of the batch kernels (one
+// translation unit per precision) and the schedule they consume.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "sfac.h"
+
+namespace sfac {
+
+// One instance as the persistent kernel sees it.
+struct BatchInst {
+    void* u;                // field (device), layout of PassArgs
+    long long npts;
+    int dim;
+    int steps;              // steps of this run
+    int n[3];
+    int items[3];           // work items of one pass along each axis
+    const void* tab[3][4];  // per axis: eC, eS, twist, twiddles (see PassArgs)
+    double jq[4];           // e^{-tau}, 1 - e^{-tau}, e^{-2 tau}, 1 - e^{-2 tau}
+};
+
+struct BatchSchedule {
+    const BatchInst* inst;
+    const long long* phase_base;   // [nphase + 1] number of the first item of each phase
+    const int* phase_step;         // [nphase]
+    const int* phase_axis;         // [nphase]
+    const long long* phase_first;  // [nphase + 1] first slot of each phase
+    const int* slot_inst;          // instance of each slot (phase, active instance)
+    const long long* slot_cum;     // inclusive running sum of items within the phase
+    int nphase;
+    int mult;                      // warp-groups per item
+    long long total_items;
+    unsigned long long* counter;   // next item to claim
+    unsigned long long* done;      // [ninst] items completed per instance
+    int* error;                    // 0, or SFAC_BATCH_TIMEOUT
+    long long spin_limit;          // polls before a wait gives up
+    int hold_instance;             // test hook: this instance's second pass never becomes ready (-1: off)
+};
+
+constexpr int SFAC_BATCH_TIMEOUT = 1;
+
+// The persistent batch kernel with `wpb` warps per CTA (<= 8) and `es` values
+// per thread for lines up to 256 points (8 or 16; FP64 always 16).
+// setup_*: set its shared-memory limit and compute the persistent grid for
+// `sms` SMs (call outside stream capture). launch_*: enqueue it on `s`.
+// cudaErrorInvalidValue for other shapes.
+cudaError_t setup_batch_f32(int wpb, int es, int sms, int* grid);
+cudaError_t setup_batch_f64(int wpb, int es, int sms, int* grid);
+cudaError_t launch_batch_f32(int wpb, int es, int grid, const BatchSchedule& sc, cudaStream_t s);
+cudaError_t launch_batch_f64(int wpb, int es, int grid, const BatchSchedule& sc, cudaStream_t s);
+
+// Items per pass of every axis of I for a kernel shape with `es` values per
+// thread below N = 512 and `mult` warp-groups per item.
+void set_items(BatchInst& I, int es, int mult);
+
+// Build the phase schedule of `inst` (fields, steps and items set) and upload
+// it into *dev (grown as needed, *cap bytes); fills `sc` except its scratch
+// pointers, spin limit and hold instance. Synchronises `st`.
+sfac_status upload_schedule(const std::vector<BatchInst>& inst, int mult, void** dev, size_t* cap,
+                            BatchSchedule* sc, cudaStream_t st);
+
+// Kernel shape `index` of the batch autotuner's list (false if out of range).
+bool batch_shape(int index, int* wpb, int* es, int* mult);
+
+}  // namespace sfac

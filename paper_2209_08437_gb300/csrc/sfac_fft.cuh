@@ -47,33 +47,51 @@ __device__ __forceinline__ C2<R> cmulc(C2<R> a, C2<R> b) {
     return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 
-// cos(pi/8), sin(pi/8), sqrt(1/2) to 20 digits.
-#define SFAC_C8 0.92387953251128675613
-#define SFAC_S8 0.38268343236508977173
-#define SFAC_R2 0.70710678118654752440
+// cos(2 pi q / 32) for q = 1 .. 7 to 21 digits (sin(2 pi q/32) = cos(2 pi (8-q)/32)).
+#define SFAC_C32_1 0.980785280403230449126
+#define SFAC_C32_2 0.923879532511286756128
+#define SFAC_C32_3 0.831469612302545237079
+#define SFAC_C32_4 0.707106781186547524401
+#define SFAC_C32_5 0.555570233019602224743
+#define SFAC_C32_6 0.382683432365089771728
+#define SFAC_C32_7 0.195090322016128267848
 
-// x * e^{-+ 2 pi i q / 16} (forward: minus sign; INV: plus sign), q in [0, 8).
+// cos(2 pi q / 32) for q in [0, 8].
+template <typename R>
+__device__ __forceinline__ R cos32(int q) {
+    switch (q) {
+        case 0: return R(1);
+        case 1: return R(SFAC_C32_1);
+        case 2: return R(SFAC_C32_2);
+        case 3: return R(SFAC_C32_3);
+        case 4: return R(SFAC_C32_4);
+        case 5: return R(SFAC_C32_5);
+        case 6: return R(SFAC_C32_6);
+        case 7: return R(SFAC_C32_7);
+        default: return R(0);
+    }
+}
+
+// v * e^{-+ 2 pi i q / 32} (forward: minus sign; INV: plus sign), q in [0, 16).
 // q is a compile-time constant after unrolling, so the branches fold away and
 // the multiplications by 1, -i and (1 -+ i)/sqrt 2 cost no general complex product.
 template <typename R, bool INV>
-__device__ __forceinline__ C2<R> rot16(C2<R> v, int q) {
-    const R c8 = R(SFAC_C8), s8 = R(SFAC_S8), r2 = R(SFAC_R2);
+__device__ __forceinline__ C2<R> rot32(C2<R> v, int q) {
     if (q == 0) return v;
-    if (q == 4) return INV ? C2<R>{-v.y, v.x} : C2<R>{v.y, -v.x};
-    if (q == 2) return INV ? C2<R>{r2 * (v.x - v.y), r2 * (v.x + v.y)}
+    if (q == 8) return INV ? C2<R>{-v.y, v.x} : C2<R>{v.y, -v.x};
+    const R r2 = R(SFAC_C32_4);
+    if (q == 4) return INV ? C2<R>{r2 * (v.x - v.y), r2 * (v.x + v.y)}
                            : C2<R>{r2 * (v.x + v.y), r2 * (v.y - v.x)};
-    if (q == 6) return INV ? C2<R>{-r2 * (v.x + v.y), r2 * (v.x - v.y)}
-                           : C2<R>{r2 * (v.y - v.x), -r2 * (v.x + v.y)};
-    R co, si;  // cos and sin of 2 pi q / 16 for odd q
-    if (q == 1) { co = c8; si = s8; }
-    else if (q == 3) { co = s8; si = c8; }
-    else if (q == 5) { co = -s8; si = c8; }
-    else { co = -c8; si = s8; }
+    if (q == 12) return INV ? C2<R>{-r2 * (v.x + v.y), r2 * (v.x - v.y)}
+                            : C2<R>{r2 * (v.y - v.x), -r2 * (v.x + v.y)};
+    // cos and sin of 2 pi q / 32
+    const R co = q < 8 ? cos32<R>(q) : -cos32<R>(16 - q);
+    const R si = q < 8 ? cos32<R>(8 - q) : cos32<R>(q - 8);
     return INV ? C2<R>{v.x * co - v.y * si, v.y * co + v.x * si}
                : C2<R>{v.x * co + v.y * si, v.y * co - v.x * si};
 }
 
-// In-register M-point DFT (M = 1, 2, 4, 8, 16), natural order in and out:
+// In-register M-point DFT (M = 1, 2, 4, ..., 32), natural order in and out:
 // y_s = sum_r x_r e^{-+2 pi i r s / M}. Radix-2 decimation in time.
 template <typename R, int M, bool INV>
 struct Dft {
@@ -88,7 +106,7 @@ struct Dft {
         Dft<R, M / 2, INV>::run(od);
 #pragma unroll
         for (int s = 0; s < M / 2; ++s) {
-            const C2<R> w = rot16<R, INV>(od[s], s * (16 / M));
+            const C2<R> w = rot32<R, INV>(od[s], s * (32 / M));
             x[s] = cadd(ev[s], w);
             x[s + M / 2] = csub(ev[s], w);
         }
@@ -99,25 +117,6 @@ struct Dft<R, 1, INV> {
     static __device__ __forceinline__ void run(C2<R>*) {}
 };
 
-// Exchange buffer of one line in shared memory. IDX_MAJOR interleaves the
-// lines of a CTA element by element (lanes of a warp walk over lines: the
-// strided-axis mapping); otherwise lines are stored one after another with a
-// pad of PAD elements (lanes walk along a line: the contiguous-axis mapping).
-template <typename R, int N, int LPC, bool IDX_MAJOR, int PAD>
-struct Exchange {
-    C2<R>* base;
-    int j;
-    __device__ __forceinline__ void put(int idx, C2<R> v) const {
-        if (IDX_MAJOR) base[idx * LPC + j] = v;
-        else base[j * (N + PAD) + idx] = v;
-    }
-    __device__ __forceinline__ C2<R> get(int idx) const {
-        return IDX_MAJOR ? base[idx * LPC + j] : base[j * (N + PAD) + idx];
-    }
-    static __device__ __forceinline__ void sync() { __syncthreads(); }
-    static constexpr int elems() { return IDX_MAJOR ? N * LPC : LPC * (N + PAD); }
-};
-
 // One Stockham pass (span P) and, recursively, the ones after it.
 // tw[m] = e^{-2 pi i m / N}, m in [0, N).
 template <typename R, int N, int E, int P, bool INV>
@@ -126,7 +125,7 @@ struct FftPass {
     static constexpr bool LAST = (P * RAD == N);
     static constexpr int T = N / E;
     static constexpr int Q = E / RAD;
-    static_assert(RAD >= 2 && (RAD & (RAD - 1)) == 0 && RAD <= 16, "radix");
+    static_assert(RAD >= 2 && (RAD & (RAD - 1)) == 0 && RAD <= 32, "radix");
 
     template <class Ex>
     static __device__ __forceinline__ void run(C2<R> (&x)[E], int t, const C2<R>* __restrict__ tw,

@@ -4,7 +4,12 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 namespace sfac {
+
+// Record the message returned by sfac_last_error() for the calling thread.
+void set_last_error(const std::string& msg);
 
 // Arguments of one fused axis pass over the field (see sfac_pass.cuh).
 //
@@ -17,6 +22,8 @@ namespace sfac {
 // Tables (device pointers, plan precision R):
 //  eC[j]  = e^{tau/2 lambda_j} / N   circulant factor incl. the inverse-FFT 1/N
 //  eS[j]  = e^{tau mu_j} / N         skew-circulant factor incl. 1/N
+//  (FP32 plans: expm1(tau/2 lambda_j) / N and expm1(tau mu_j) / N, the
+//   increments the FP32 passes add; see sfac_pass.cuh)
 //  twist  = N complex e^{i pi k / N} (interleaved re, im)
 //  twid   = N complex e^{-2 pi i m / N}
 // J^Q_s(v) = v / sqrt(E + (1 - E) v^2) with E = e^{-2 s} is applied to every

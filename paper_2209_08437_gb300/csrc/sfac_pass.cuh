@@ -12,6 +12,13 @@
 //   FFT, * e^{tau/2 lambda}/N, IFFT
 // with the spectra of Remark 1, all in registers between shared-memory
 // exchanges of the Stockham passes (sfac_fft.cuh).
+//
+// Two kernel shapes share that chain:
+//  - axis_pass_kernel: a line's T = N/E threads may span several warps, so the
+//    exchanges synchronise the CTA (any N, both precisions);
+//  - axis_pass_warp_kernel: E = 16 or 32 values per thread, so a line of
+//    N <= 1024 points lives inside one warp (with 32/T lines per warp); the
+//    exchanges need only warp-level synchronisation (FP32, 32 <= N <= 1024).
 #pragma once
 
 #include "sfac_fft.cuh"
@@ -36,12 +43,227 @@ __device__ __forceinline__ R jq_flow(R v, R E, R omE) {
     return v * rsqrt_r(fma(v * v, omE, E));
 }
 
+// Increment of J^Q for the FP32 passes: with q = (1 - E)(1 - v)(1 + v) the
+// flow is v / sqrt(1 - q) = v + v q / (s (1 + s)), s = sqrt(1 - q); this returns
+// the added term v q / (s (1 + s)), which is small, so its rounding is too.
+template <typename R>
+__device__ __forceinline__ R jq_increment(R v, R omE) {
+    const R q = omE * (R(1) - v) * (R(1) + v);
+    const R s = sqrt(R(1) - q);
+    return v * q / (s * (R(1) + s));
+}
+
 template <typename R>
 __device__ __forceinline__ C2<R> ldg_c2(const C2<R>* p) {
     using V = typename Vec2T<R>::type;
     const V v = __ldg(reinterpret_cast<const V*>(p));
     return {v.x, v.y};
 }
+
+template <typename R, int E>
+__device__ __forceinline__ void jq_all(C2<R> (&x)[E], double E0d, double omd) {
+    const R E0 = R(E0d), om = R(omd);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        x[e].x = jq_flow(x[e].x, E0, om);
+        x[e].y = jq_flow(x[e].y, E0, om);
+    }
+}
+
+// x <- F^{-1} diag(m) F x for the line held in x (m includes the 1/N).
+template <typename R, int N, int E, class Ex>
+__device__ __forceinline__ void apply_spectral(C2<R> (&x)[E], int t, const C2<R>* __restrict__ tw,
+                                               const Ex& ex, const R* __restrict__ m) {
+    constexpr int T = N / E;
+    line_fft<R, N, E, false>(x, t, tw, ex);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const R s = __ldg(m + t + e * T);
+        x[e].x *= s;
+        x[e].y *= s;
+    }
+    line_fft<R, N, E, true>(x, t, tw, ex);
+}
+
+// e^{tau/2 C} e^{tau S} e^{tau/2 C} on the line held in x (FP64 passes; the
+// tables hold e^{t lambda} / N).
+template <typename R, int N, int E, class Ex>
+__device__ __forceinline__ void two_level_chain(C2<R> (&x)[E], int t, const PassArgs& a, const Ex& ex) {
+    constexpr int T = N / E;
+    const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
+    const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
+    // e^{tau/2 C}
+    apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eC));
+    // e^{tau S} = Theta^{-1} F^{-1} e^{tau Lambda_S} F Theta
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = cmul(x[e], ldg_c2(twist + t + e * T));
+    apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eS));
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = cmulc(x[e], ldg_c2(twist + t + e * T));
+    // e^{tau/2 C}
+    apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eC));
+}
+
+// The whole FP32 pass in increment form. The loaded line x0 is kept as it is
+// and every change the pass makes is summed in d:
+//   J^Q (load)  d += v q / (s (1 + s))                        (jq_increment)
+//   e^{t C}     d += F^{-1} (expm1(t lambda)/N) F (x0 + d)
+//   e^{tau S}   d += Theta^{-1} F^{-1} (expm1(tau mu)/N) F Theta (x0 + d)
+//   J^Q (store) d += its increment at x0 + d
+// and the result x0 + d is rounded once. Each increment is small against x0,
+// so its FP32 rounding is too, and the field itself is rounded once per pass
+// instead of after every factor. The tables hold expm1(t lambda) / N.
+template <typename R, int N, int E, class Ex>
+__device__ __forceinline__ void two_level_pass_incr(C2<R> (&x0)[E], int t, const PassArgs& a, const Ex& ex) {
+    constexpr int T = N / E;
+    const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
+    const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
+    const R* __restrict__ eC = static_cast<const R*>(a.eC);
+    const R* __restrict__ eS = static_cast<const R*>(a.eS);
+    C2<R> d[E], y[E];
+    if (a.jq_in) {
+        const R om = R(a.jq_in_1mE);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            d[e] = {jq_increment(x0[e].x, om), jq_increment(x0[e].y, om)};
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) d[e] = {R(0), R(0)};
+    }
+    // e^{tau/2 C}
+#pragma unroll
+    for (int e = 0; e < E; ++e) y[e] = cadd(x0[e], d[e]);
+    apply_spectral<R, N, E>(y, t, tw, ex, eC);
+#pragma unroll
+    for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
+    // e^{tau S}
+#pragma unroll
+    for (int e = 0; e < E; ++e) y[e] = cmul(cadd(x0[e], d[e]), ldg_c2(twist + t + e * T));
+    apply_spectral<R, N, E>(y, t, tw, ex, eS);
+#pragma unroll
+    for (int e = 0; e < E; ++e) d[e] = cadd(d[e], cmulc(y[e], ldg_c2(twist + t + e * T)));
+    // e^{tau/2 C}
+#pragma unroll
+    for (int e = 0; e < E; ++e) y[e] = cadd(x0[e], d[e]);
+    apply_spectral<R, N, E>(y, t, tw, ex, eC);
+#pragma unroll
+    for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
+    if (a.jq_out) {
+        const R om = R(a.jq_out_1mE);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const C2<R> w = cadd(x0[e], d[e]);
+            d[e].x += jq_increment(w.x, om);
+            d[e].y += jq_increment(w.y, om);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) x0[e] = cadd(x0[e], d[e]);
+}
+
+// One whole pass on the line held in x: FP32 in increment form, FP64 plain.
+template <typename R, int N, int E, class Ex>
+__device__ __forceinline__ void fused_pass(C2<R> (&x)[E], int t, const PassArgs& a, const Ex& ex) {
+    if constexpr (sizeof(R) == 4) {
+        two_level_pass_incr<R, N, E>(x, t, a, ex);
+    } else {
+        if (a.jq_in) jq_all<R, E>(x, a.jq_in_E, a.jq_in_1mE);
+        two_level_chain<R, N, E>(x, t, a, ex);
+        if (a.jq_out) jq_all<R, E>(x, a.jq_out_E, a.jq_out_1mE);
+    }
+}
+
+// Global addressing of complex line `cl` (see PassArgs): element idx of the
+// line is (p0[idx], p1[idx]) for a contiguous pass and the 2-vector at
+// p0 + idx * stride for a strided pass.
+// Field loads: plain (may be served by L1) or .cg (L2 only). A persistent kernel
+// that reads data another SM wrote during the same launch uses .cg.
+template <bool CG, typename T>
+__device__ __forceinline__ T ld_field(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+template <typename R, int N, bool STRIDED>
+struct LineRef {
+    R* p0;
+    R* p1;
+    long long stride;
+    bool active;
+
+    __device__ __forceinline__ LineRef(const PassArgs& a, long long cl) {
+        R* u = static_cast<R*>(a.u);
+        active = cl < a.clines;
+        if (STRIDED) {
+            const long long pairs = a.inner >> 1;
+            const long long o = active ? cl / pairs : 0;
+            const long long c = active ? cl - o * pairs : 0;
+            p0 = u + o * (long long)N * a.inner + 2 * c;
+            p1 = nullptr;
+            stride = a.inner;
+        } else {
+            const long long r0 = active ? 2 * cl : 0;
+            p0 = u + r0 * N;
+            p1 = (active && r0 + 1 < a.outer) ? p0 + N : nullptr;
+            stride = 1;
+        }
+    }
+
+    template <int E, bool CG = false>
+    __device__ __forceinline__ void load(C2<R> (&x)[E], int t) const {
+        using V = typename Vec2T<R>::type;
+        constexpr int T = N / E;
+        if (STRIDED) {
+            const R* q = p0 + t * stride;
+            const long long step = T * stride;
+#pragma unroll
+            for (int e = 0; e < E; ++e, q += step) {
+                if (active) {
+                    const V v = ld_field<CG>(reinterpret_cast<const V*>(q));
+                    x[e] = {v.x, v.y};
+                } else {
+                    x[e] = {R(0), R(0)};
+                }
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = t + e * T;
+                x[e].x = active ? ld_field<CG>(p0 + idx) : R(0);
+                x[e].y = p1 ? ld_field<CG>(p1 + idx) : R(0);
+            }
+        }
+    }
+
+    template <int E>
+    __device__ __forceinline__ void store(const C2<R> (&x)[E], int t) const {
+        using V = typename Vec2T<R>::type;
+        constexpr int T = N / E;
+        if (!active) return;
+        if (STRIDED) {
+            R* q = p0 + t * stride;
+            const long long step = T * stride;
+#pragma unroll
+            for (int e = 0; e < E; ++e, q += step) {
+                V v;
+                v.x = x[e].x;
+                v.y = x[e].y;
+                *reinterpret_cast<V*>(q) = v;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = t + e * T;
+                p0[idx] = x[e].x;
+                if (p1) p1[idx] = x[e].y;
+            }
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Kernel 1: CTA-synchronised exchanges.
+// ---------------------------------------------------------------------------
 
 // Shared-memory exchange with a bank-spreading pad: element a is stored at
 // a + (a >> LOG) where 2^LOG complex values fill 128 bytes.
@@ -60,150 +282,102 @@ struct PadExchange {
     static constexpr int elems() { return N * LPC + ((N * LPC) >> LOG) + 1; }
 };
 
-template <typename R, int N, int E, int LPC, bool STRIDED>
-__global__ void __launch_bounds__(LPC*(N / E))
+// MINB: minimum resident CTAs per SM the register allocation must allow.
+template <typename R, int N, int E, int LPC, bool STRIDED, int MINB>
+__global__ void __launch_bounds__(LPC*(N / E), MINB)
 axis_pass_kernel(const PassArgs a) {
     constexpr int T = N / E;
     using Ex = PadExchange<R, N, LPC, STRIDED>;
-    using V = typename Vec2T<R>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
     const int tid = threadIdx.x;
+    // Strided passes: lanes walk over neighbouring lines first (coalesced rows);
+    // contiguous passes: lanes walk along a line.
     const int j = STRIDED ? (tid % LPC) : (tid / T);
     const int t = STRIDED ? (tid / LPC) : (tid % T);
-    const long long cl = (long long)blockIdx.x * LPC + j;
-    const bool active = cl < a.clines;
+    const LineRef<R, N, STRIDED> line(a, (long long)blockIdx.x * LPC + j);
     const Ex ex{reinterpret_cast<C2<R>*>(smem_raw), j};
 
-    R* __restrict__ u = static_cast<R*>(a.u);
-    const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
-    const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
-    const R* __restrict__ eC = static_cast<const R*>(a.eC);
-    const R* __restrict__ eS = static_cast<const R*>(a.eS);
-
-    // ---- load (and J^Q) -------------------------------------------------
     C2<R> x[E];
-    R* p0;
-    R* p1 = nullptr;
-    long long stride = 1;
-    if (STRIDED) {
-        const long long pairs = a.inner >> 1;
-        const long long o = active ? cl / pairs : 0;
-        const long long c = active ? cl - o * pairs : 0;
-        p0 = u + o * (long long)N * a.inner + 2 * c;
-        stride = a.inner;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int idx = t + e * T;
-            if (active) {
-                const V v = *reinterpret_cast<const V*>(p0 + idx * stride);
-                x[e] = {v.x, v.y};
-            } else {
-                x[e] = {R(0), R(0)};
-            }
-        }
-    } else {
-        const long long r0 = active ? 2 * cl : 0;
-        const bool has1 = active && (r0 + 1 < a.outer);
-        p0 = u + r0 * N;
-        p1 = has1 ? p0 + N : nullptr;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int idx = t + e * T;
-            x[e].x = active ? p0[idx] : R(0);
-            x[e].y = has1 ? p1[idx] : R(0);
-        }
-    }
-    if (a.jq_in) {
-        const R E0 = R(a.jq_in_E), om = R(a.jq_in_1mE);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            x[e].x = jq_flow(x[e].x, E0, om);
-            x[e].y = jq_flow(x[e].y, E0, om);
-        }
-    }
-
-    // ---- e^{tau/2 C} ------------------------------------------------------
-    line_fft<R, N, E, false>(x, t, tw, ex);
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const R s = __ldg(eC + t + e * T);
-        x[e].x *= s;
-        x[e].y *= s;
-    }
-    line_fft<R, N, E, true>(x, t, tw, ex);
-    // ---- e^{tau S} = Theta^{-1} F^{-1} e^{tau Lambda_S} F Theta -------------
-#pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = cmul(x[e], ldg_c2(twist + t + e * T));
-    line_fft<R, N, E, false>(x, t, tw, ex);
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const R s = __ldg(eS + t + e * T);
-        x[e].x *= s;
-        x[e].y *= s;
-    }
-    line_fft<R, N, E, true>(x, t, tw, ex);
-#pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = cmulc(x[e], ldg_c2(twist + t + e * T));
-    // ---- e^{tau/2 C} ------------------------------------------------------
-    line_fft<R, N, E, false>(x, t, tw, ex);
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const R s = __ldg(eC + t + e * T);
-        x[e].x *= s;
-        x[e].y *= s;
-    }
-    line_fft<R, N, E, true>(x, t, tw, ex);
-
-    // ---- (J^Q and) store --------------------------------------------------
-    if (a.jq_out) {
-        const R E0 = R(a.jq_out_E), om = R(a.jq_out_1mE);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            x[e].x = jq_flow(x[e].x, E0, om);
-            x[e].y = jq_flow(x[e].y, E0, om);
-        }
-    }
-    if (!active) return;
-    if (STRIDED) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int idx = t + e * T;
-            V v;
-            v.x = x[e].x;
-            v.y = x[e].y;
-            *reinterpret_cast<V*>(p0 + idx * stride) = v;
-        }
-    } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int idx = t + e * T;
-            p0[idx] = x[e].x;
-            if (p1) p1[idx] = x[e].y;
-        }
-    }
+    line.template load<E>(x, t);
+    fused_pass<R, N, E>(x, t, a, ex);
+    line.template store<E>(x, t);
 }
 
-// Elements per thread: 8 for most lengths (radix-8 passes), 16 from N = 2048.
+// ---------------------------------------------------------------------------
+// Kernel 2: warp-local lines (E = 32).
+// ---------------------------------------------------------------------------
+
+// Per-line exchange region of N + N/E complex values: element a is stored at
+// a + a/E. With lanes laid out as (line, t), the first-pass writes (at t*E + r)
+// and the reads (at t + e*T) of every pass hit distinct banks in each
+// half-warp, also when a half-warp holds several short lines.
+template <typename R, int N, int E>
+struct WarpExchange {
+    static constexpr int SH = E == 32 ? 5 : (E == 16 ? 4 : 3);
+    C2<R>* base;
+    __device__ __forceinline__ void put(int idx, C2<R> v) const { base[idx + (idx >> SH)] = v; }
+    __device__ __forceinline__ C2<R> get(int idx) const { return base[idx + (idx >> SH)]; }
+    static __device__ __forceinline__ void sync() { __syncwarp(); }
+    static constexpr int LINE_ELEMS = N + N / E;
+};
+
+// Lines [first, first + 32/T) of the pass `a`, processed by one warp. `region`
+// is this warp's shared memory: (32/T) * (N + N/E) complex values.
+template <typename R, int N, int E, bool STRIDED, bool CG>
+__device__ __forceinline__ void warp_pass_lines(const PassArgs& a, long long first, C2<R>* region, int lane) {
+    constexpr int T = N / E;
+    static_assert(T >= 1 && T <= 32, "line must fit one warp");
+    using Ex = WarpExchange<R, N, E>;
+    const int j = lane / T, t = lane % T;
+    const LineRef<R, N, STRIDED> line(a, first + j);
+    const Ex ex{region + j * Ex::LINE_ELEMS};
+    C2<R> x[E];
+    line.template load<E, CG>(x, t);
+    fused_pass<R, N, E>(x, t, a, ex);
+    line.template store<E>(x, t);
+}
+
+template <typename R, int N, int E, int WPB, bool STRIDED>
+__global__ void __launch_bounds__(WPB * 32)
+axis_pass_warp_kernel(const PassArgs a) {
+    constexpr int LPW = 32 / (N / E);  // lines per warp
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C2<R>* region = reinterpret_cast<C2<R>*>(smem_raw) + warp * LPW * WarpExchange<R, N, E>::LINE_ELEMS;
+    warp_pass_lines<R, N, E, STRIDED, false>(a, ((long long)blockIdx.x * WPB + warp) * LPW, region, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Launch configuration
+// ---------------------------------------------------------------------------
+
+// Elements per thread of kernel 1: 8 for most lengths (radix-8 passes), 16 from N = 2048.
 template <int N>
 constexpr int elems_per_thread() {
     return N >= 2048 ? 16 : (N < 8 ? N : 8);
 }
 
-template <typename R, int N, int LPC, bool STRIDED>
+template <class K>
+cudaError_t set_smem(K kern, size_t smem, bool& configured) {
+    if (configured) return cudaSuccess;
+    const cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess) configured = true;
+    return err;
+}
+
+template <typename R, int N, int E, int LPC, bool STRIDED>
 cudaError_t launch_cfg(const PassArgs& a, cudaStream_t s) {
-    constexpr int E = elems_per_thread<N>();
     constexpr int T = N / E;
+    // FP64 with 128-thread CTAs: at least two CTAs per SM, so one CTA's
+    // exchanges overlap the other's FP64 arithmetic.
+    constexpr int MINB = (sizeof(R) == 8 && LPC * T == 128) ? 2 : 1;
     using Ex = PadExchange<R, N, LPC, STRIDED>;
     const size_t smem = sizeof(C2<R>) * (size_t)Ex::elems();
-    auto kern = axis_pass_kernel<R, N, E, LPC, STRIDED>;
+    auto kern = axis_pass_kernel<R, N, E, LPC, STRIDED, MINB>;
     static bool configured = false;
-    if (!configured) {
-        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
-        if (err != cudaSuccess) return err;
-        configured = true;
-    }
+    cudaError_t err = set_smem(kern, smem, configured);
+    if (err != cudaSuccess) return err;
     const long long grid = (a.clines + LPC - 1) / LPC;
     if (grid <= 0) return cudaSuccess;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -211,18 +385,49 @@ cudaError_t launch_cfg(const PassArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <typename R, int N, int E, int WPB, bool STRIDED>
+cudaError_t launch_warp(const PassArgs& a, cudaStream_t s) {
+    constexpr int LPC = WPB * (32 / (N / E));
+    const size_t smem = sizeof(C2<R>) * (size_t)LPC * WarpExchange<R, N, E>::LINE_ELEMS;
+    auto kern = axis_pass_warp_kernel<R, N, E, WPB, STRIDED>;
+    static bool configured = false;
+    cudaError_t err = set_smem(kern, smem, configured);
+    if (err != cudaSuccess) return err;
+    const long long grid = (a.clines + LPC - 1) / LPC;
+    if (grid <= 0) return cudaSuccess;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    kern<<<(unsigned)grid, WPB * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename R, int N>
 cudaError_t launch_n(const PassArgs& a, cudaStream_t s) {
     constexpr int E = elems_per_thread<N>();
     constexpr int T = N / E;
-    // Strided passes: at least 32 bytes of each row per CTA (one sector);
-    // both mappings aim at about 256 threads per CTA.
-    // (Lines of 2048+ points keep 256 threads per CTA and take one line pair.)
-    constexpr int MIN_S = (T >= 256) ? 1 : 32 / (2 * (int)sizeof(R));
-    constexpr int LPC_S = (256 / T) > MIN_S ? (256 / T) : MIN_S;
-    constexpr int LPC_C = (256 / T) > 1 ? (256 / T) : 1;
-    if (a.inner > 1) return launch_cfg<R, N, LPC_S, true>(a, s);
-    return launch_cfg<R, N, LPC_C, false>(a, s);
+    if constexpr (sizeof(R) == 4 && N >= 32 && N <= 512) {
+        // FP32: warp-local lines with 16 values per thread. Two warps per CTA
+        // for long lines (few lines: many small CTAs spread better over 152
+        // SMs), four otherwise.
+        constexpr int WPB = N >= 512 ? 2 : 4;
+        if (a.inner > 1) return launch_warp<R, N, 16, WPB, true>(a, s);
+        return launch_warp<R, N, 16, WPB, false>(a, s);
+    } else if constexpr (sizeof(R) == 4 && N >= 1024) {
+        // FP32, long lines: 16 values per thread and one line per CTA (64 to
+        // 256 threads), which keeps the increment form's two arrays in registers.
+        if (a.inner > 1) return launch_cfg<R, N, 16, 1, true>(a, s);
+        return launch_cfg<R, N, 16, 1, false>(a, s);
+    } else {
+        // FP64 passes are bound by the FP64 pipe, not by memory: they take
+        // 128-thread CTAs (several per SM, so one CTA's exchanges overlap
+        // another's arithmetic). FP32 strided passes keep >= 32 bytes of each row
+        // per CTA (one sector); lines of 2048+ points keep 256 threads per CTA.
+        constexpr int TPB = sizeof(R) == 8 ? 128 : 256;
+        constexpr int MIN_S = (T >= 256 || sizeof(R) == 8) ? 1 : 32 / (2 * (int)sizeof(R));
+        constexpr int LPC_S = (TPB / T) > MIN_S ? (TPB / T) : MIN_S;
+        constexpr int LPC_C = (TPB / T) > 1 ? (TPB / T) : 1;
+        if (a.inner > 1) return launch_cfg<R, N, E, LPC_S, true>(a, s);
+        return launch_cfg<R, N, E, LPC_C, false>(a, s);
+    }
 }
 
 template <typename R>

@@ -10,7 +10,12 @@
 #include <vector>
 
 #include "sfac.h"
+#include "sfac_host.h"
 #include "sfac_internal.h"
+
+using sfac::AxisHost;
+using sfac::compute_axis;
+using sfac::is_pow2;
 
 namespace {
 
@@ -21,131 +26,16 @@ sfac_status fail(sfac_status st, const std::string& msg) {
     return st;
 }
 
+}  // namespace
+
+namespace sfac {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace sfac
+
+namespace {
+
 sfac_status cuda_fail(cudaError_t err, const char* what) {
     return fail(SFAC_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
-}
-
-bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
-
-// ---------------------------------------------------------------------------
-// FP64 precompute (Sec. 2.1, Sec. 2.2, Remark 1)
-// ---------------------------------------------------------------------------
-
-// cos(pi m / n) and sin(pi m / n) for integer m, reduced exactly to an angle in
-// [0, pi/4] first so that every table entry is correctly rounded or nearly so.
-void sincospi_frac(long long m, long long n, double* c, double* s) {
-    const long long two_n = 2 * n;
-    m %= two_n;
-    if (m < 0) m += two_n;
-    double sc = 1.0, ss = 1.0;
-    if (m >= n) {  // theta - pi
-        m -= n;
-        sc = -sc;
-        ss = -ss;
-    }
-    if (2 * m > n) {  // pi - theta
-        m = n - m;
-        sc = -sc;
-    }
-    // theta = pi m / n in [0, pi/2]
-    double cv, sv;
-    if (4 * m > n) {  // theta = pi/2 - phi, phi = pi (n - 2m) / (2n) in [0, pi/4)
-        const double phi = M_PI * (double)(n - 2 * m) / (double)(2 * n);
-        cv = std::sin(phi);
-        sv = std::cos(phi);
-    } else {
-        const double th = M_PI * (double)m / (double)n;
-        cv = std::cos(th);
-        sv = std::sin(th);
-    }
-    *c = sc * cv;
-    *s = ss * sv;
-}
-
-// Compensated (Neumaier) summation.
-struct KahanSum {
-    double s = 0.0, c = 0.0;
-    void add(double v) {
-        const double t = s + v;
-        if (std::fabs(s) >= std::fabs(v)) c += (s - t) + v;
-        else c += (v - t) + s;
-        s = t;
-    }
-    double value() const { return s + c; }
-};
-
-struct AxisHost {
-    int n = 0;
-    std::vector<double> bcol, cfirst, sfirst, lambda, mu;
-    std::vector<double> eC, eS, twist, twid;  // twist, twid: interleaved complex
-};
-
-// Tables of one axis: omega_k by eqs. (g_coe), (omega_coe); b_k by eq. (B);
-// c_k, s_k by eqs. (C), (S); spectra by Remark 1; exponentials for tau.
-void compute_axis(double alpha, double eps, double tau, double a, double b, int n, AxisHost* T) {
-    T->n = n;
-    const double h = (b - a) / (double)(n + 1);
-    // g_{k+1} = (1 - (alpha+1)/(k+1)) g_k; omega_0 = alpha/2 g_0;
-    // omega_{k+1} = alpha/2 g_{k+1} + (2-alpha)/2 g_k
-    std::vector<double> g(n + 2), w(n + 2);
-    g[0] = 1.0;
-    for (int k = 0; k + 1 < n + 2; ++k) g[k + 1] = (1.0 - (alpha + 1.0) / (double)(k + 1)) * g[k];
-    w[0] = 0.5 * alpha * g[0];
-    for (int k = 0; k + 1 < n + 2; ++k) w[k + 1] = 0.5 * alpha * g[k + 1] + 0.5 * (2.0 - alpha) * g[k];
-    // B = r (D + D^T), r = -eps^2 / (2 h^alpha cos(alpha pi / 2)) > 0:
-    // b_0 = 2 r omega_1, b_1 = r (omega_0 + omega_2), b_k = r omega_{k+1} (k >= 2).
-    const double r = -eps * eps / (2.0 * std::pow(h, alpha) * std::cos(alpha * M_PI / 2.0));
-    T->bcol.assign(n, 0.0);
-    T->bcol[0] = 2.0 * r * w[1];
-    if (n > 1) T->bcol[1] = r * (w[0] + w[2]);
-    for (int k = 2; k < n; ++k) T->bcol[k] = r * w[k + 1];
-    // B is symmetric, b_{-k} = b_k, so b_{k-m+1} = b_{-(n-k)} = b_{n-k} with n = m-1:
-    // c_k = (b_k + b_{n-k}) / 2, s_k = (b_k - b_{n-k}) / 2 (k >= 1), c_0 = s_0 = b_0 / 2.
-    T->cfirst.assign(n, 0.0);
-    T->sfirst.assign(n, 0.0);
-    T->cfirst[0] = 0.5 * T->bcol[0];
-    T->sfirst[0] = 0.5 * T->bcol[0];
-    for (int k = 1; k < n; ++k) {
-        T->cfirst[k] = 0.5 * (T->bcol[k] + T->bcol[n - k]);
-        T->sfirst[k] = 0.5 * (T->bcol[k] - T->bcol[n - k]);
-    }
-    // cos / sin of pi m / n for m in [0, 2n)
-    std::vector<double> cs(2 * n), sn(2 * n);
-    for (int m = 0; m < 2 * n; ++m) sincospi_frac(m, n, &cs[m], &sn[m]);
-    // lambda_j = sum_k c_k e^{-2 pi i jk/n}; mu_j = sum_k s_k e^{i pi k/n} e^{-2 pi i jk/n}
-    //         = sum_k s_k e^{-i pi k (2j-1)/n}. Both are real because C and S are
-    // symmetric (c_k = c_{n-k}, s_{-k} = -s_{n-k}); the real parts are summed.
-    T->lambda.assign(n, 0.0);
-    T->mu.assign(n, 0.0);
-    const long long two_n = 2LL * n;
-    for (int j = 0; j < n; ++j) {
-        KahanSum sl, sm;
-        for (int k = 0; k < n; ++k) {
-            const long long ml = (2LL * j * k) % two_n;
-            long long mm = ((long long)k * (2LL * j - 1)) % two_n;
-            if (mm < 0) mm += two_n;
-            sl.add(T->cfirst[k] * cs[ml]);
-            sm.add(T->sfirst[k] * cs[mm]);
-        }
-        T->lambda[j] = sl.value();
-        T->mu[j] = sm.value();
-    }
-    // Factors with the inverse-FFT normalisation 1/n folded in.
-    T->eC.resize(n);
-    T->eS.resize(n);
-    for (int j = 0; j < n; ++j) {
-        T->eC[j] = std::exp(0.5 * tau * T->lambda[j]) / (double)n;
-        T->eS[j] = std::exp(tau * T->mu[j]) / (double)n;
-    }
-    // Twist e^{i pi k/n} and FFT twiddles e^{-2 pi i m/n}.
-    T->twist.resize(2 * n);
-    T->twid.resize(2 * n);
-    for (int k = 0; k < n; ++k) {
-        T->twist[2 * k] = cs[k];
-        T->twist[2 * k + 1] = sn[k];
-        T->twid[2 * k] = cs[(2 * k) % (2 * n)];
-        T->twid[2 * k + 1] = -sn[(2 * k) % (2 * n)];
-    }
 }
 
 sfac_status validate(const sfac_params* p, bool need_supported) {
@@ -326,7 +216,9 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
         return fail(SFAC_ENOMEM, "host allocation failed");
     }
     for (int l = 0; l < params->dim; ++l) {
-        const std::vector<double>* src[4] = {&host[l].eC, &host[l].eS, &host[l].twist, &host[l].twid};
+        const bool f64 = params->prec == SFAC_FP64;
+        const std::vector<double>* src[4] = {f64 ? &host[l].eC : &host[l].dC, f64 ? &host[l].eS : &host[l].dS,
+                                             &host[l].twist, &host[l].twid};
         for (int q = 0; q < 4; ++q) {
             unsigned char* dst = blob.data() + off[l][q];
             const std::vector<double>& v = *src[q];

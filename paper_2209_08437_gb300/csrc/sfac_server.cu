@@ -1,0 +1,369 @@
+// sfac_server.cu - continuous batching of SFAC solves (sfac_server_* in sfac.h).
+//
+// A server owns one device arena. Each admitted request gets a slot: its field
+// and its per-axis tables live in the arena until the result is fetched.
+// Rounds advance every active slot by up to `chunk` steps in one persistent
+// launch of the batch kernel (sfac_batch.cuh), so requests admitted while a
+// round runs join the next round and their work overlaps on the device with
+// everyone else's. Admission and result copies use an internal copy stream, so
+// they overlap with a running round.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sfac.h"
+#include "sfac_batch_launch.h"
+#include "sfac_host.h"
+#include "sfac_internal.h"
+
+namespace {
+
+sfac_status sfail(sfac_status st, const std::string& msg) {
+    sfac::set_last_error(msg);
+    return st;
+}
+
+sfac_status scuda(cudaError_t err, const char* what) {
+    return sfail(SFAC_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
+}
+
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Slot {
+    bool used = false;
+    sfac_params p{};
+    sfac::BatchInst inst{};
+    size_t off = 0, bytes = 0;  // arena allocation
+    long long remaining = 0, done = 0;
+};
+
+// First-fit allocator over [0, size) with coalescing frees.
+struct Arena {
+    std::map<size_t, size_t> free_blocks;  // offset -> size
+    size_t total = 0, used = 0;
+    void init(size_t size) {
+        free_blocks.clear();
+        free_blocks[0] = size;
+        total = size;
+        used = 0;
+    }
+    bool alloc(size_t bytes, size_t* off) {
+        for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t noff = it->first + bytes;
+                free_blocks.erase(it);
+                if (rest) free_blocks[noff] = rest;
+                used += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        auto it = free_blocks.emplace(off, bytes).first;
+        auto next = std::next(it);
+        if (next != free_blocks.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_blocks.erase(next);
+        }
+        if (it != free_blocks.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_blocks.erase(it);
+            }
+        }
+        used -= bytes;
+    }
+    size_t largest_free() const {
+        size_t m = 0;
+        for (const auto& kv : free_blocks) m = std::max(m, kv.second);
+        return m;
+    }
+};
+
+size_t real_bytes(int prec) { return prec == SFAC_FP64 ? 8 : 4; }
+
+// Arena bytes one request needs: its field and four tables per axis.
+size_t request_bytes(const sfac_params& p) {
+    const size_t rs = real_bytes(p.prec);
+    size_t pts = 1;
+    for (int a = 0; a < p.dim; ++a) pts *= (size_t)p.n[a];
+    size_t b = al256(pts * rs);
+    for (int a = 0; a < p.dim; ++a) b += 2 * al256((size_t)p.n[a] * rs) + 2 * al256(2 * (size_t)p.n[a] * rs);
+    return b;
+}
+
+sfac_status check_request(const sfac_params* p, int prec) {
+    if (!p) return sfail(SFAC_EINVAL, "params is NULL");
+    if (p->dim != 2 && p->dim != 3) return sfail(SFAC_EUNSUPPORTED, "served problems must be 2D or 3D");
+    if (p->reserved != 0) return sfail(SFAC_EINVAL, "reserved field must be 0");
+    if (p->prec != prec) return sfail(SFAC_EINVAL, "request precision differs from the server's");
+    if (!(std::isfinite(p->eps) && p->eps > 0) || !(std::isfinite(p->tau) && p->tau > 0))
+        return sfail(SFAC_EINVAL, "eps and tau must be finite and > 0");
+    if (!(std::isfinite(p->a) && std::isfinite(p->b) && p->b > p->a)) return sfail(SFAC_EINVAL, "need finite a < b");
+    for (int l = 0; l < p->dim; ++l) {
+        if (!(p->alpha[l] > 1.0 && p->alpha[l] < 2.0)) return sfail(SFAC_EINVAL, "alpha[l] must lie in (1, 2)");
+        if (!sfac::is_pow2(p->n[l]) || p->n[l] < 32 || p->n[l] > 512)
+            return sfail(SFAC_EUNSUPPORTED, "served grid lengths must be powers of two in [32, 512]");
+    }
+    return SFAC_OK;
+}
+
+}  // namespace
+
+struct sfac_server {
+    int device = 0, sms = 0, prec = SFAC_FP32;
+    void* arena_mem = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+    cudaStream_t copy_stream = nullptr;
+    void* dev_sched = nullptr;
+    size_t sched_cap = 0;
+    unsigned long long* scratch = nullptr;  // counter, done[max_slots], error
+    int* host_error = nullptr;
+    sfac::BatchSchedule sc{};
+    int shape = 0, grid = 0;
+    bool in_flight = false;
+    std::vector<int> round_slots;
+    std::vector<long long> round_steps;
+    long long spin_limit = 20000000;
+};
+
+extern "C" {
+
+sfac_status sfac_server_create(size_t arena_bytes, int max_slots, int prec, void* stream, sfac_server** out) {
+    (void)stream;
+    if (!out) return sfail(SFAC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (arena_bytes < 4096 || max_slots < 1 || (prec != SFAC_FP32 && prec != SFAC_FP64))
+        return sfail(SFAC_EINVAL, "need arena_bytes >= 4096, max_slots >= 1 and a valid precision");
+    sfac_server* S = new (std::nothrow) sfac_server();
+    if (!S) return sfail(SFAC_ENOMEM, "host allocation failed");
+    S->prec = prec;
+    cudaGetDevice(&S->device);
+    cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device);
+    cudaError_t err = cudaMalloc(&S->arena_mem, arena_bytes);
+    if (err == cudaSuccess)
+        err = cudaMalloc(reinterpret_cast<void**>(&S->scratch), sizeof(unsigned long long) * (size_t)(max_slots + 2));
+    if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void**>(&S->host_error), sizeof(int));
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        sfac_server_destroy(S);
+        return sfail(SFAC_ENOMEM, std::string("server allocation: ") + cudaGetErrorString(err));
+    }
+    *S->host_error = 0;
+    S->arena.init(arena_bytes);
+    S->slots.resize(max_slots);
+    *out = S;
+    return SFAC_OK;
+}
+
+sfac_status sfac_server_destroy(sfac_server* S) {
+    if (!S) return SFAC_OK;
+    cudaDeviceSynchronize();
+    if (S->arena_mem) cudaFree(S->arena_mem);
+    if (S->scratch) cudaFree(S->scratch);
+    if (S->dev_sched) cudaFree(S->dev_sched);
+    if (S->host_error) cudaFreeHost(S->host_error);
+    if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
+    delete S;
+    return SFAC_OK;
+}
+
+sfac_status sfac_server_request_bytes(const sfac_params* params, size_t* bytes) {
+    if (!params || !bytes) return sfail(SFAC_EINVAL, "NULL argument");
+    const sfac_status st = check_request(params, params->prec);
+    if (st != SFAC_OK) return st;
+    *bytes = request_bytes(*params);
+    return SFAC_OK;
+}
+
+sfac_status sfac_server_admit(sfac_server* S, const sfac_params* params, const void* u0_host, long long nsteps,
+                              int* slot_out) {
+    if (!S || !u0_host || !slot_out) return sfail(SFAC_EINVAL, "NULL argument");
+    *slot_out = -1;
+    sfac_status st = check_request(params, S->prec);
+    if (st != SFAC_OK) return st;
+    if (nsteps < 0 || nsteps > (1LL << 30)) return sfail(SFAC_EINVAL, "nsteps out of range");
+    int slot = -1;
+    for (int i = 0; i < (int)S->slots.size(); ++i)
+        if (!S->slots[i].used) {
+            slot = i;
+            break;
+        }
+    if (slot < 0) return sfail(SFAC_ENOMEM, "no free slot");
+    const size_t bytes = request_bytes(*params);
+    size_t off = 0;
+    if (!S->arena.alloc(bytes, &off)) return sfail(SFAC_ENOMEM, "device arena full");
+    // FP64 tables on the host, then one copy of field + tables into the arena.
+    const sfac_params& p = *params;
+    const bool f64 = p.prec == SFAC_FP64;
+    const size_t rs = real_bytes(p.prec);
+    size_t pts = 1;
+    for (int a = 0; a < p.dim; ++a) pts *= (size_t)p.n[a];
+    std::vector<unsigned char> blob(bytes, 0);
+    std::memcpy(blob.data(), u0_host, pts * rs);
+    Slot& s = S->slots[slot];
+    s = Slot();
+    s.inst.dim = p.dim;
+    s.inst.npts = (long long)pts;
+    size_t cur = al256(pts * rs);
+    unsigned char* base = static_cast<unsigned char*>(S->arena_mem) + off;
+    try {
+        for (int a = 0; a < 3; ++a) {
+            s.inst.n[a] = a < p.dim ? p.n[a] : 1;
+            if (a >= p.dim) continue;
+            sfac::AxisHost H;
+            sfac::compute_axis(p.alpha[a], p.eps, p.tau, p.a, p.b, p.n[a], &H);
+            const std::vector<double>* src[4] = {f64 ? &H.eC : &H.dC, f64 ? &H.eS : &H.dS, &H.twist, &H.twid};
+            for (int q = 0; q < 4; ++q) {
+                unsigned char* dst = blob.data() + cur;
+                if (f64) {
+                    std::memcpy(dst, src[q]->data(), src[q]->size() * sizeof(double));
+                } else {
+                    float* f = reinterpret_cast<float*>(dst);
+                    for (size_t k = 0; k < src[q]->size(); ++k) f[k] = (float)(*src[q])[k];
+                }
+                s.inst.tab[a][q] = base + cur;
+                cur += al256(src[q]->size() * rs);
+            }
+        }
+    } catch (const std::bad_alloc&) {
+        S->arena.release(off, bytes);
+        return sfail(SFAC_ENOMEM, "host allocation failed");
+    }
+    s.inst.u = base;
+    s.inst.jq[0] = std::exp(-p.tau);
+    s.inst.jq[1] = -std::expm1(-p.tau);
+    s.inst.jq[2] = std::exp(-2.0 * p.tau);
+    s.inst.jq[3] = -std::expm1(-2.0 * p.tau);
+    cudaError_t err = cudaMemcpyAsync(base, blob.data(), bytes, cudaMemcpyHostToDevice, S->copy_stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(S->copy_stream);
+    if (err != cudaSuccess) {
+        S->arena.release(off, bytes);
+        return scuda(err, "request upload");
+    }
+    s.used = true;
+    s.p = p;
+    s.off = off;
+    s.bytes = bytes;
+    s.remaining = nsteps;
+    s.done = 0;
+    *slot_out = slot;
+    return SFAC_OK;
+}
+
+sfac_status sfac_server_round(sfac_server* S, long long chunk, int shape, void* stream) {
+    if (!S || chunk < 1) return sfail(SFAC_EINVAL, "need a server and chunk >= 1");
+    if (S->in_flight) return sfail(SFAC_EINVAL, "a round is already in flight (call sfac_server_wait)");
+    int wpb = 0, es = 0, mult = 0;
+    if (!sfac::batch_shape(shape, &wpb, &es, &mult)) return sfail(SFAC_EINVAL, "bad kernel shape index");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    S->round_slots.clear();
+    S->round_steps.clear();
+    std::vector<sfac::BatchInst> inst;
+    for (int i = 0; i < (int)S->slots.size(); ++i) {
+        Slot& s = S->slots[i];
+        if (!s.used || s.remaining <= 0) continue;
+        const long long k = std::min(chunk, s.remaining);
+        sfac::BatchInst I = s.inst;
+        I.steps = (int)k;
+        sfac::set_items(I, es, mult);
+        inst.push_back(I);
+        S->round_slots.push_back(i);
+        S->round_steps.push_back(k);
+    }
+    *S->host_error = 0;
+    S->in_flight = true;
+    if (inst.empty()) return SFAC_OK;
+    sfac_status r = sfac::upload_schedule(inst, mult, &S->dev_sched, &S->sched_cap, &S->sc, st);
+    if (r != SFAC_OK) {
+        S->in_flight = false;
+        return r;
+    }
+    S->sc.counter = S->scratch;
+    S->sc.done = S->scratch + 1;
+    S->sc.error = reinterpret_cast<int*>(S->scratch + 1 + (long long)S->slots.size());
+    S->sc.spin_limit = S->spin_limit;
+    S->sc.hold_instance = -1;
+    cudaError_t err = S->prec == SFAC_FP64 ? sfac::setup_batch_f64(wpb, es, S->sms, &S->grid)
+                                           : sfac::setup_batch_f32(wpb, es, S->sms, &S->grid);
+    if (err == cudaSuccess)
+        err = cudaMemsetAsync(S->scratch, 0, sizeof(unsigned long long) * (S->slots.size() + 2), st);
+    if (err == cudaSuccess)
+        err = S->prec == SFAC_FP64 ? sfac::launch_batch_f64(wpb, es, S->grid, S->sc, st)
+                                   : sfac::launch_batch_f32(wpb, es, S->grid, S->sc, st);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(S->host_error, S->sc.error, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (err != cudaSuccess) {
+        S->in_flight = false;
+        return scuda(err, "round launch");
+    }
+    return SFAC_OK;
+}
+
+sfac_status sfac_server_wait(sfac_server* S, void* stream, int* finished, int max_finished, int* nfinished) {
+    if (!S || !nfinished || (max_finished > 0 && !finished)) return sfail(SFAC_EINVAL, "NULL argument");
+    *nfinished = 0;
+    if (!S->in_flight) return SFAC_OK;
+    cudaError_t err = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    S->in_flight = false;
+    if (err != cudaSuccess) return scuda(err, "round synchronise");
+    if (*S->host_error != 0) return sfail(SFAC_ETIMEOUT, "a dependency wait gave up");
+    int nf = 0;
+    for (size_t k = 0; k < S->round_slots.size(); ++k) {
+        Slot& s = S->slots[S->round_slots[k]];
+        s.remaining -= S->round_steps[k];
+        s.done += S->round_steps[k];
+        if (s.remaining == 0) {
+            if (nf < max_finished) finished[nf] = S->round_slots[k];
+            ++nf;
+        }
+    }
+    *nfinished = nf;
+    return SFAC_OK;
+}
+
+sfac_status sfac_server_fetch(sfac_server* S, int slot, void* u_host, int release) {
+    if (!S || slot < 0 || slot >= (int)S->slots.size() || !S->slots[slot].used)
+        return sfail(SFAC_EINVAL, "bad server or slot");
+    Slot& s = S->slots[slot];
+    const bool in_round = S->in_flight &&
+                          std::find(S->round_slots.begin(), S->round_slots.end(), slot) != S->round_slots.end();
+    if (in_round) return sfail(SFAC_EINVAL, "slot is part of the round in flight");
+    if (u_host) {
+        const size_t bytes = (size_t)s.inst.npts * real_bytes(S->prec);
+        cudaError_t err = cudaMemcpyAsync(u_host, s.inst.u, bytes, cudaMemcpyDeviceToHost, S->copy_stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(S->copy_stream);
+        if (err != cudaSuccess) return scuda(err, "result copy");
+    }
+    if (release) {
+        S->arena.release(s.off, s.bytes);
+        s = Slot();
+    }
+    return SFAC_OK;
+}
+
+sfac_status sfac_server_info(const sfac_server* S, size_t* free_bytes, size_t* largest_free, int* active,
+                             int* capacity) {
+    if (!S) return sfail(SFAC_EINVAL, "server is NULL");
+    if (free_bytes) *free_bytes = S->arena.total - S->arena.used;
+    if (largest_free) *largest_free = S->arena.largest_free();
+    int n = 0;
+    for (const Slot& s : S->slots) n += s.used ? 1 : 0;
+    if (active) *active = n;
+    if (capacity) *capacity = (int)S->slots.size();
+    return SFAC_OK;
+}
+
+}  // extern "C"

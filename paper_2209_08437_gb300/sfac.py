@@ -59,6 +59,27 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sfac_step_host": (ctypes.c_int, [vp, vp, ll, vp]),
         "sfac_axis_pass": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]),
         "sfac_plan_tables": (ctypes.c_int, [P(SfacParams), ctypes.c_int, P(d), P(d), P(d), P(d)]),
+        "sfac_batch_create": (ctypes.c_int, [P(SfacParams), ctypes.c_int, vp, P(vp)]),
+        "sfac_batch_destroy": (ctypes.c_int, [vp]),
+        "sfac_batch_prepare": (ctypes.c_int, [vp, P(vp), P(ll), vp]),
+        "sfac_batch_launch": (ctypes.c_int, [vp, vp]),
+        "sfac_batch_wait": (ctypes.c_int, [vp, vp]),
+        "sfac_batch_step": (ctypes.c_int, [vp, P(vp), P(ll), vp]),
+        "sfac_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, vp, P(ctypes.c_int)]),
+        "sfac_batch_set_config": (ctypes.c_int, [vp, ctypes.c_int]),
+        "sfac_batch_get_config": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
+                                                 P(ctypes.c_int)]),
+        "sfac_batch_num_configs": (ctypes.c_int, []),
+        "sfac_batch_set_wait_limit": (ctypes.c_int, [vp, ll, ctypes.c_int]),
+        "sfac_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, vp, P(vp)]),
+        "sfac_server_destroy": (ctypes.c_int, [vp]),
+        "sfac_server_request_bytes": (ctypes.c_int, [P(SfacParams), P(ctypes.c_size_t)]),
+        "sfac_server_admit": (ctypes.c_int, [vp, P(SfacParams), vp, ll, P(ctypes.c_int)]),
+        "sfac_server_round": (ctypes.c_int, [vp, ll, ctypes.c_int, vp]),
+        "sfac_server_wait": (ctypes.c_int, [vp, vp, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]),
+        "sfac_server_fetch": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
+        "sfac_server_info": (ctypes.c_int, [vp, P(ctypes.c_size_t), P(ctypes.c_size_t), P(ctypes.c_int),
+                                            P(ctypes.c_int)]),
         "sfac_last_error": (ctypes.c_char_p, []),
         "sfac_version": (ctypes.c_int, []),
     }
@@ -164,7 +185,212 @@ def sfac_version() -> int:
     return load().sfac_version()
 
 
-# ---- convenience wrapper -------------------------------------------------------
+def _ptr_array(fields):
+    arr = (ctypes.c_void_p * len(fields))()
+    for i, f in enumerate(fields):
+        arr[i] = _ptr(f)
+    return arr
+
+
+def _steps_array(nsteps):
+    arr = (ctypes.c_longlong * len(nsteps))()
+    for i, v in enumerate(nsteps):
+        arr[i] = int(v)
+    return arr
+
+
+def sfac_batch_create(params_list, stream=None) -> int:
+    arr = (SfacParams * len(params_list))(*params_list)
+    out = ctypes.c_void_p()
+    _check(load().sfac_batch_create(arr, len(params_list), _stream(stream), ctypes.byref(out)), "sfac_batch_create")
+    return out.value
+
+
+def sfac_batch_destroy(batch: int) -> None:
+    _check(load().sfac_batch_destroy(batch), "sfac_batch_destroy")
+
+
+def sfac_batch_prepare(batch: int, fields, nsteps, stream=None) -> None:
+    _check(load().sfac_batch_prepare(batch, _ptr_array(fields), _steps_array(nsteps), _stream(stream)),
+           "sfac_batch_prepare")
+
+
+def sfac_batch_launch(batch: int, stream=None) -> None:
+    _check(load().sfac_batch_launch(batch, _stream(stream)), "sfac_batch_launch")
+
+
+def sfac_batch_wait(batch: int, stream=None) -> None:
+    _check(load().sfac_batch_wait(batch, _stream(stream)), "sfac_batch_wait")
+
+
+def sfac_batch_step(batch: int, fields, nsteps, stream=None) -> None:
+    _check(load().sfac_batch_step(batch, _ptr_array(fields), _steps_array(nsteps), _stream(stream)),
+           "sfac_batch_step")
+
+
+def sfac_batch_autotune(batch: int, max_steps: int, stream=None) -> int:
+    choice = ctypes.c_int(-1)
+    _check(load().sfac_batch_autotune(batch, int(max_steps), _stream(stream), ctypes.byref(choice)),
+           "sfac_batch_autotune")
+    return choice.value
+
+
+def sfac_batch_set_config(batch: int, config: int) -> None:
+    _check(load().sfac_batch_set_config(batch, int(config)), "sfac_batch_set_config")
+
+
+def sfac_batch_get_config(batch: int):
+    vals = [ctypes.c_int() for _ in range(4)]
+    _check(load().sfac_batch_get_config(batch, *[ctypes.byref(v) for v in vals]), "sfac_batch_get_config")
+    return tuple(v.value for v in vals)
+
+
+def sfac_batch_num_configs() -> int:
+    return load().sfac_batch_num_configs()
+
+
+def sfac_batch_set_wait_limit(batch: int, spin_limit: int, hold_instance: int = -1) -> None:
+    _check(load().sfac_batch_set_wait_limit(batch, int(spin_limit), int(hold_instance)),
+           "sfac_batch_set_wait_limit")
+
+
+def sfac_server_create(arena_bytes: int, max_slots: int, prec: int = SFAC_FP32, stream=None) -> int:
+    out = ctypes.c_void_p()
+    _check(load().sfac_server_create(int(arena_bytes), int(max_slots), int(prec), _stream(stream),
+                                     ctypes.byref(out)), "sfac_server_create")
+    return out.value
+
+
+def sfac_server_destroy(server: int) -> None:
+    _check(load().sfac_server_destroy(server), "sfac_server_destroy")
+
+
+def sfac_server_request_bytes(params: SfacParams) -> int:
+    out = ctypes.c_size_t()
+    _check(load().sfac_server_request_bytes(ctypes.byref(params), ctypes.byref(out)), "sfac_server_request_bytes")
+    return out.value
+
+
+def sfac_server_admit(server: int, params: SfacParams, u0_host, nsteps: int):
+    """Slot number, or None when no slot or arena block is free (SFAC_ENOMEM)."""
+    slot = ctypes.c_int(-1)
+    st = load().sfac_server_admit(server, ctypes.byref(params), _ptr(u0_host), int(nsteps), ctypes.byref(slot))
+    if st == SFAC_ENOMEM:
+        return None
+    _check(st, "sfac_server_admit")
+    return slot.value
+
+
+def sfac_server_round(server: int, chunk: int, shape: int = 0, stream=None) -> None:
+    _check(load().sfac_server_round(server, int(chunk), int(shape), _stream(stream)), "sfac_server_round")
+
+
+def sfac_server_wait(server: int, capacity: int, stream=None):
+    buf = (ctypes.c_int * max(capacity, 1))()
+    n = ctypes.c_int(0)
+    _check(load().sfac_server_wait(server, _stream(stream), buf, capacity, ctypes.byref(n)), "sfac_server_wait")
+    return [buf[i] for i in range(min(n.value, capacity))]
+
+
+def sfac_server_fetch(server: int, slot: int, u_host=None, release: bool = True) -> None:
+    _check(load().sfac_server_fetch(server, int(slot), _ptr(u_host) if u_host is not None else None,
+                                    1 if release else 0), "sfac_server_fetch")
+
+
+def sfac_server_info(server: int) -> dict:
+    fb, lf, act, cap = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+    _check(load().sfac_server_info(server, ctypes.byref(fb), ctypes.byref(lf), ctypes.byref(act),
+                                   ctypes.byref(cap)), "sfac_server_info")
+    return {"free_bytes": fb.value, "largest_free": lf.value, "active": act.value, "capacity": cap.value}
+
+
+# ---- convenience wrappers ------------------------------------------------------
+
+class Server:
+    """Owns one sfac_server (continuous batching of requests of different sizes)."""
+
+    def __init__(self, arena_bytes: int, max_slots: int, prec: int = SFAC_FP32, stream=None):
+        self.prec, self.capacity = prec, int(max_slots)
+        self.handle = sfac_server_create(arena_bytes, max_slots, prec, stream)
+
+    def admit(self, problem, u0_host, nsteps: int):
+        p = make_params(problem.n, problem.alpha, problem.eps, problem.tau, problem.a, problem.b, self.prec)
+        return sfac_server_admit(self.handle, p, u0_host, nsteps)
+
+    def round(self, chunk: int, shape: int = 0, stream=None):
+        sfac_server_round(self.handle, chunk, shape, stream)
+
+    def wait(self, stream=None):
+        return sfac_server_wait(self.handle, self.capacity, stream)
+
+    def fetch(self, slot: int, u_host=None, release: bool = True):
+        sfac_server_fetch(self.handle, slot, u_host, release)
+
+    def info(self) -> dict:
+        return sfac_server_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sfac_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns one sfac_batch: many independent problems in one persistent launch.
+    `problems` are sfac_inputs.Problem-like objects (n, alpha, eps, tau, a, b)."""
+
+    def __init__(self, problems, prec: int = SFAC_FP32, stream=None):
+        self.params = [make_params(p.n, p.alpha, p.eps, p.tau, p.a, p.b, prec) for p in problems]
+        self.shapes = [tuple(reversed(tuple(int(v) for v in p.n))) for p in problems]
+        self.prec = prec
+        self.handle = sfac_batch_create(self.params, stream)
+
+    def step(self, fields, nsteps, stream=None):
+        sfac_batch_step(self.handle, fields, nsteps, stream)
+
+    def prepare(self, fields, nsteps, stream=None):
+        sfac_batch_prepare(self.handle, fields, nsteps, stream)
+
+    def launch(self, stream=None):
+        sfac_batch_launch(self.handle, stream)
+
+    def wait(self, stream=None):
+        sfac_batch_wait(self.handle, stream)
+
+    def autotune(self, max_steps: int = 10, stream=None) -> int:
+        return sfac_batch_autotune(self.handle, max_steps, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sfac_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+
 
 class Plan:
     """Owns one sfac_plan. The field is a contiguous CUDA tensor of shape

@@ -84,16 +84,30 @@ def test_config1_full_run():
     assert rel_err(gpu_run(prob, u0, prob.steps), ref) <= TOL64
 
 
-def test_config2_full_run():
-    """2D n=1024, alpha=(1.3,1.7), eps=0.05, tau=1e-3, the full 1000 steps, against
-    the oracle's spectral route (its dense route alone drifts by ~3e-12 over 1000
-    steps from its own rounding; the spectral route stays within ~1e-15 per step)."""
+@pytest.fixture(scope="module")
+def config2_reference():
+    """The full 1000-step config-2 run of the oracle's spectral route (its dense
+    route alone drifts by ~3e-12 over 1000 steps from its own rounding; the
+    spectral route stays within ~1e-15 per application)."""
+    return O.solve(I.CONFIG2, I.config2_u0(), route="spectral")
+
+
+def test_config2_full_run(config2_reference):
+    """2D n=1024, alpha=(1.3,1.7), eps=0.05, tau=1e-3, the full 1000 steps."""
     prob = I.CONFIG2
-    u0 = I.config2_u0()
-    ref = O.solve(prob, u0, route="spectral")
-    err = rel_err(gpu_run(prob, u0, prob.steps), ref)
+    err = rel_err(gpu_run(prob, I.config2_u0(), prob.steps), config2_reference)
     print(f"config2 FP64 rel err vs spectral oracle {err:.3e}")
     assert err <= TOL64
+
+
+def test_config2_full_run_fp32(config2_reference):
+    """The FP32 path over the full 1000 steps: max-norm error against the FP64
+    oracle at most 1e-5."""
+    prob = I.CONFIG2
+    u32 = np.asarray(I.config2_u0(), dtype=np.float32).astype(np.float64)
+    err = float(np.abs(gpu_run(prob, u32, prob.steps, S.SFAC_FP32) - config2_reference).max())
+    print(f"config2 FP32 1000 steps max-norm error {err:.3e}")
+    assert err <= 1e-5
 
 
 def test_config2_first_100_steps_dense():
