@@ -303,6 +303,41 @@ def run_batched(args, S, torch):
     return 0
 
 
+def run_serving(args, S, torch):
+    """Poisson stream of 2000 requests (200/s; half 2D n in {64..512}, half 3D n in
+    {32,64,128}; 100-1000 steps; FP32) served with continuous batching: requests
+    are admitted by device memory into a 2 GiB arena and advanced in rounds of
+    `chunk` steps by the persistent batch kernel."""
+    reqs = I.serving_stream(args.requests)
+    chunk = args.chunk
+    S.load()
+    with S.Server(2 << 30, 1024, S.SFAC_FP32) as srv:
+        # warm-up: a few small requests
+        S.serve(I.serving_stream(8, rate_hz=1e6, sizes_2d=(64,), sizes_3d=(32,), steps_range=(5, 10)),
+                lambda r: np.asarray(I.request_u0(r), np.float32), srv, chunk=chunk)
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        out = S.serve(reqs, lambda r: np.asarray(I.request_u0(r), np.float32), srv, chunk=chunk)
+        clocks = sampler.stop()
+    lat = np.array(list(out["latency"].values()))
+    line = {
+        "metric": METRIC, "value": out["throughput"], "unit": UNIT, "n_gpus": 1, "steps": out["rounds"],
+        "warmup": 1, "ms_per_step": 1e3 * out["wall_s"] / max(out["rounds"], 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson stream of {len(reqs)} requests at 200/s, half 2D n in "
+                               "{64,128,256,512}, half 3D n in {32,64,128}, alpha U[1.1,1.9], eps U[0.02,0.2], "
+                               "tau=1e-3, 100-1000 steps, FP32; continuous batching in rounds of "
+                               f"{chunk} steps, admission by a 2 GiB device arena",
+                   "requests": len(reqs), "chunk_steps": chunk},
+        "latency": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                    "mean_s": float(lat.mean()), "max_s": float(lat.max())},
+        "served_point_steps": out["point_steps"], "wall_s": out["wall_s"], "rounds": out["rounds"],
+        "clocks": clocks, "gpu_launches": out["rounds"],
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -342,7 +377,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sfac", choices=["sfac", "reference"])
-    ap.add_argument("--workload", default="2d1024", choices=sorted(WORKLOADS) + ["batch512"])
+    ap.add_argument("--workload", default="2d1024", choices=sorted(WORKLOADS) + ["batch512", "serve"])
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--chunk", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--parity-steps", type=int, default=50)
     args = ap.parse_args()
@@ -364,6 +401,8 @@ def main():
         torch.cuda.set_device(0)
     if args.workload == "batch512":
         return run_batched(args, S, torch)
+    if args.workload == "serve":
+        return run_serving(args, S, torch)
     w = WORKLOADS[args.workload]
     problem = w["problem"]
     u0 = w["u0"]()
