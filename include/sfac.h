@@ -193,6 +193,27 @@ int sfac_batch_num_configs(void);
  * effect at the next prepare. */
 sfac_status sfac_batch_set_wait_limit(sfac_batch* batch, long long spin_limit, int hold_instance);
 
+/* Largest batch sfac_batch_launch_noalloc accepts. */
+#define SFAC_NOALLOC_MAX_INSTANCES 8192
+
+/* No counterpart in the paper: a deployment convenience. Same as
+ * sfac_batch_launch, but allocating nothing: the persistent kernel's work
+ * counter, per-instance completion counters and status word live in one fixed
+ * array of (SFAC_NOALLOC_MAX_INSTANCES + 2) * 8 bytes = 64 KiB of device memory
+ * that the library holds on every GPU it is loaded on until the process exits.
+ * For callers that must not call cudaMalloc when they launch work (an
+ * allocator that owns all device memory, latency-critical loops where
+ * allocation may synchronise the device, fixed memory budgets). The batch must
+ * be prepared (its tables and schedule were allocated by sfac_batch_create and
+ * sfac_batch_prepare); the caller's fields are the inputs and outputs. Batches
+ * of more than SFAC_NOALLOC_MAX_INSTANCES instances are rejected with
+ * SFAC_EINVAL. All calls on a device share the array: each call clears the
+ * counters first, and calls whose work overlaps on the GPU race, so serialise
+ * them. The first call on each device looks up the array's device address
+ * (with the batch's device made current); make that first call before any
+ * stream capture. Report status with sfac_batch_wait as for sfac_batch_launch. */
+sfac_status sfac_batch_launch_noalloc(sfac_batch* batch, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of requests of different sizes.              */
 /* ------------------------------------------------------------------------ */

@@ -6,7 +6,8 @@ from .sfac import (SFAC_FP32, SFAC_FP64, Batch, Plan, Server, SfacError, SfacPar
                    sfac_solve, sfac_step, sfac_step_host, sfac_version, sfac_batch_create,
                    sfac_batch_destroy, sfac_batch_prepare, sfac_batch_launch, sfac_batch_wait,
                    sfac_batch_step, sfac_batch_autotune, sfac_batch_set_config, sfac_batch_get_config,
-                   sfac_batch_num_configs, sfac_batch_set_wait_limit, sfac_server_create,
+                   sfac_batch_num_configs, sfac_batch_set_wait_limit, sfac_batch_launch_noalloc,
+                   sfac_server_create,
                    sfac_server_destroy, sfac_server_request_bytes, sfac_server_admit, sfac_server_round,
                    sfac_server_wait, sfac_server_fetch, sfac_server_info)
 from .serving import serve  # noqa: F401

@@ -246,6 +246,33 @@ sfac_status launch(sfac_batch* B, cudaStream_t st) {
 
 }  // namespace
 
+namespace sfac {
+
+// The prepared run of B with its scratch counters at `scratch` (work counter,
+// B->count completion counters, status word) instead of B's own; used by
+// sfac_batch_launch_noalloc. Clears the counters, launches, copies the status.
+sfac_status batch_launch_with_scratch(sfac_batch* B, unsigned long long* scratch, cudaStream_t st) {
+    if (!B->prepared) return bfail(SFAC_EINVAL, "batch is not prepared (call sfac_batch_prepare)");
+    BatchSchedule sc = B->sched;
+    sc.counter = scratch;
+    sc.done = scratch + 1;
+    sc.error = reinterpret_cast<int*>(scratch + 1 + B->count);
+    cudaError_t err = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (size_t)(B->count + 2), st);
+    if (err != cudaSuccess) return bcuda(err, "scratch reset");
+    if (sc.total_items > 0) {
+        err = dispatch_batch(B->prec, kConfigs[B->config], B->grid, sc, st);
+        if (err != cudaSuccess) return bcuda(err, "batch kernel launch");
+    }
+    err = cudaMemcpyAsync(B->host_error, sc.error, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (err != cudaSuccess) return bcuda(err, "error flag copy");
+    return SFAC_OK;
+}
+
+int batch_count(const sfac_batch* B) { return B->count; }
+int batch_device(const sfac_batch* B) { return B->device; }
+
+}  // namespace sfac
+
 extern "C" {
 
 sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream, sfac_batch** out) {

@@ -71,6 +71,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                                  P(ctypes.c_int)]),
         "sfac_batch_num_configs": (ctypes.c_int, []),
         "sfac_batch_set_wait_limit": (ctypes.c_int, [vp, ll, ctypes.c_int]),
+        "sfac_batch_launch_noalloc": (ctypes.c_int, [vp, vp]),
         "sfac_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, vp, P(vp)]),
         "sfac_server_destroy": (ctypes.c_int, [vp]),
         "sfac_server_request_bytes": (ctypes.c_int, [P(SfacParams), P(ctypes.c_size_t)]),
@@ -217,6 +218,12 @@ def sfac_batch_prepare(batch: int, fields, nsteps, stream=None) -> None:
 
 def sfac_batch_launch(batch: int, stream=None) -> None:
     _check(load().sfac_batch_launch(batch, _stream(stream)), "sfac_batch_launch")
+
+
+def sfac_batch_launch_noalloc(batch: int, stream=None) -> None:
+    """sfac_batch_launch without any allocation: the counters live in the
+    library's fixed device array (for callers that cannot allocate at launch)."""
+    _check(load().sfac_batch_launch_noalloc(batch, _stream(stream)), "sfac_batch_launch_noalloc")
 
 
 def sfac_batch_wait(batch: int, stream=None) -> None:
