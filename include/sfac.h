@@ -76,11 +76,20 @@ typedef struct sfac_plan sfac_plan;
  * mu_j = sum_k s_k e^{i pi k/n} e^{-2 pi i jk/n} by Remark 1; the tables
  * e^{tau/2 lambda_j}/n, e^{tau mu_j}/n, e^{i pi k/n}, e^{-2 pi i m/n}), then one
  * upload of those tables to the current device on `stream`.
- * Supported grid lengths: every n[l] a power of two with 4 <= n[l] <= 4096.
- * Other lengths return SFAC_EUNSUPPORTED. The plan owns its device tables and
+ * Supported grid lengths: powers of two 4 <= n[l] <= 4096 (FFTs of length n),
+ * and any 2 <= n[l] <= 2048 otherwise: then e^{tau/2 C} and e^{tau S}, both
+ * symmetric Toeplitz matrices, are applied as linear convolutions with their
+ * first columns, zero-padded to a power of two L >= 2n - 1 (real multipliers,
+ * no twist); an axis whose stride is odd takes that path too. Other lengths
+ * return SFAC_EUNSUPPORTED. The plan owns its device tables and
  * any staging buffer; free it with sfac_plan_destroy. On success *out is set;
  * on failure *out is NULL. The call synchronises `stream` once (upload). */
 sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan** out);
+
+/* How the plan runs axis `axis` (0-based): *fft_len receives the FFT length of
+ * its pass (n, or the padded length L) and *padded 1 for the zero-padded
+ * convolution pass, 0 for the spectral pass with the twist. */
+sfac_status sfac_plan_info(const sfac_plan* plan, int axis, int* fft_len, int* padded);
 
 /* Release a plan and its device memory. Synchronises the device first so that no
  * enqueued work still reads the tables. NULL is accepted (no-op). */
@@ -111,6 +120,15 @@ sfac_status sfac_solve(sfac_plan* plan, void* u_dev, double T, void* stream);
  * exposes one such launch so that callers can time or test it alone.
  * SFAC_EINVAL for a bad axis, mode or pointer. */
 sfac_status sfac_axis_pass(sfac_plan* plan, void* u_dev, int axis, int jq_in, int jq_out, void* stream);
+
+/* Monitoring reductions (Examples 4 and 5, Sec. 5): out[0] = max |u| and
+ * out[1] = the discrete energy E(u) = h^d ( (1/4) sum (u^2 - 1)^2
+ * - (1/2) u^T A u ), h^d the product of the axes' h, A u = sum_l B_l along axis l.
+ * u^T A u is accumulated line by line as x . B_l x with B_l x formed through the
+ * spectra of C_l and S_l (zero-padded axes: one linear convolution with B_l's
+ * column); FP64 arithmetic for both precisions; partial sums are added in a
+ * fixed order (deterministic). u_dev is read only. Synchronises `stream`. */
+sfac_status sfac_diagnostics(sfac_plan* plan, const void* u_dev, double* out, void* stream);
 
 /* End-to-end variant on HOST memory: copy u_host (plan precision, layout above)
  * to a plan-owned device buffer, advance it by nsteps, copy it back into u_host.

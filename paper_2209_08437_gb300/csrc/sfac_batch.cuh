@@ -135,6 +135,7 @@ batch_kernel(const BatchSchedule b) {
         pa.inner = inner;
         pa.outer = I.npts / ((long long)N * inner);
         pa.clines = (a == 0) ? (pa.outer + 1) / 2 : pa.outer * (inner / 2);
+        pa.nmem = N;
         pa.eC = I.tab[a][0];
         pa.eS = I.tab[a][1];
         pa.twist = I.tab[a][2];

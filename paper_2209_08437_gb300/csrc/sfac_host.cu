@@ -1,5 +1,6 @@
 // sfac_host.cu - FP64 precompute of the per-axis tables (host code).
 #include <cmath>
+#include <utility>
 
 #include "sfac_host.h"
 
@@ -55,7 +56,99 @@ struct KahanSum {
     double value() const { return s + c; }
 };
 
+// In-place iterative radix-2 FFT (forward, e^{-2 pi i jk/L}) of L = 2^k complex
+// values, FP64, with exactly reduced twiddles.
+void fft_pow2(std::vector<double>& re, std::vector<double>& im) {
+    const int L = (int)re.size();
+    for (int i = 1, j = 0; i < L; ++i) {
+        int bit = L >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            std::swap(re[i], re[j]);
+            std::swap(im[i], im[j]);
+        }
+    }
+    for (int len = 2; len <= L; len <<= 1) {
+        const int half = len >> 1;
+        for (int k = 0; k < half; ++k) {
+            double c, s;
+            sincospi_frac(2LL * k, len, &c, &s);  // angle 2 pi k / len
+            const double wr = c, wi = -s;
+            for (int i = k; i < L; i += len) {
+                const double xr = re[i + half] * wr - im[i + half] * wi;
+                const double xi = re[i + half] * wi + im[i + half] * wr;
+                re[i + half] = re[i] - xr;
+                im[i + half] = im[i] - xi;
+                re[i] += xr;
+                im[i] += xi;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+int padded_length(int n) {
+    int L = 4;
+    while (L < 2 * n - 1) L <<= 1;
+    return L;
+}
+
+void compute_axis_padded(const AxisHost& T, double tau, AxisPadded* P) {
+    const int n = T.n;
+    const int L = padded_length(n);
+    P->n = n;
+    P->L = L;
+    std::vector<double> cs(2 * n), sn(2 * n);
+    for (int m = 0; m < 2 * n; ++m) sincospi_frac(m, n, &cs[m], &sn[m]);
+    // First columns of e^{t C} - I and e^{tau S} - I from expm1 of the spectra:
+    //   g_d = (1/n) sum_j expm1(t lambda_j) cos(2 pi j d / n),     d = 0 .. n-1
+    //   h_d = (1/n) sum_j expm1(tau mu_j) cos(pi d (2j - 1) / n),  d = 0 .. n-1 (h_{-d} = h_d)
+    // (the identity's share sum_j cos(...) vanishes for d != 0 mod n).
+    std::vector<double> xc(n), xs(n), g1(n), h1(n);
+    for (int j = 0; j < n; ++j) {
+        xc[j] = std::expm1(0.5 * tau * T.lambda[j]);
+        xs[j] = std::expm1(tau * T.mu[j]);
+    }
+    const long long two_n = 2LL * n;
+    for (int d = 0; d < n; ++d) {
+        KahanSum sg, sh;
+        for (int j = 0; j < n; ++j) {
+            sg.add(xc[j] * cs[(2LL * j * d) % two_n]);
+            long long mm = ((long long)d * (2LL * j - 1)) % two_n;
+            if (mm < 0) mm += two_n;
+            sh.add(xs[j] * cs[mm]);
+        }
+        g1[d] = sg.value() / n;
+        h1[d] = sh.value() / n;
+    }
+    // Padded, symmetric columns: offset d in (-n, n) at index d mod L. The
+    // circulant part repeats its column with period n (c_d = g_{d mod n}).
+    auto spectrum = [&](const std::vector<double>& col, bool circulant, double diag_add, std::vector<double>* out) {
+        std::vector<double> re(L, 0.0), im(L, 0.0);
+        for (int d = -(n - 1); d <= n - 1; ++d) {
+            const int src = circulant ? ((d % n) + n) % n : (d < 0 ? -d : d);
+            re[(d % L + L) % L] = col[src];
+        }
+        re[0] += diag_add;
+        fft_pow2(re, im);
+        out->resize(L);
+        for (int k = 0; k < L; ++k) (*out)[k] = re[k] / (double)L;  // real: the column is symmetric
+    };
+    spectrum(T.bcol, false, 0.0, &P->mB);
+    spectrum(g1, true, 1.0, &P->mC);
+    spectrum(h1, false, 1.0, &P->mS);
+    spectrum(g1, true, 0.0, &P->mC1);
+    spectrum(h1, false, 0.0, &P->mS1);
+    P->twid.resize(2 * L);
+    for (int k = 0; k < L; ++k) {
+        double c, s;
+        sincospi_frac(2LL * k, L, &c, &s);
+        P->twid[2 * k] = c;
+        P->twid[2 * k + 1] = -s;
+    }
+}
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 

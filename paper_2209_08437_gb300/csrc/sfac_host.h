@@ -13,7 +13,25 @@ struct AxisHost {
     std::vector<double> dC, dS;               // expm1 forms for the FP32 increment passes
 };
 
+// Zero-padded form of one axis, for any n: e^{t C} and e^{tau S} are symmetric
+// Toeplitz matrices, so each is a linear convolution of the line with its
+// first column; padded to a power of two L >= 2n - 1 the convolution is
+// circular and its multiplier (the DFT of the symmetric padded column) is real.
+struct AxisPadded {
+    int n = 0, L = 0;
+    std::vector<double> mC, mS;    // L real multipliers incl. 1/L: e^{tau/2 C}, e^{tau S}
+    std::vector<double> mC1, mS1;  // the same for (e^{tX} - I): increment forms
+    std::vector<double> mB;        // L real multipliers incl. 1/L of B itself (diagnostics)
+    std::vector<double> twid;      // L complex e^{-2 pi i m / L}, interleaved
+};
+
 bool is_pow2(int v);
+
+// Smallest power of two >= 2n - 1 (at least 4).
+int padded_length(int n);
+
+// Padded tables of one axis (needs the spectra of compute_axis in T).
+void compute_axis_padded(const AxisHost& T, double tau, AxisPadded* P);
 
 // Tables of one axis for Riesz order alpha, interface parameter eps, step tau,
 // domain [a, b] and n interior unknowns.

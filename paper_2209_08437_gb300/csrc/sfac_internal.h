@@ -33,6 +33,7 @@ struct PassArgs {
     long long outer;
     long long inner;
     long long clines;  // number of complex lines
+    int nmem;          // line length in memory: N, or n < N for a zero-padded pass
     const void* eC;
     const void* eS;
     const void* twist;
@@ -46,5 +47,13 @@ struct PassArgs {
 // Returns cudaErrorInvalidValue for an unsupported N.
 cudaError_t launch_pass_f64(int N, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_pass_f32(int N, const PassArgs& a, cudaStream_t s);
+
+// Zero-padded pass: lines of a.nmem < N points, FFT length N = L (a power of two
+// >= 2 nmem - 1, in [4, 4096]). The tables are then eC = multiplier of e^{tau/2 C}
+// and eS = multiplier of e^{tau S} as linear convolutions (real, incl. 1/L;
+// increment forms for FP32), twist = NULL, twid = L twiddles. Each factor is
+// FFT, multiply, inverse FFT, zero the values past nmem.
+cudaError_t launch_pass_padded_f64(int N, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_pass_padded_f32(int N, const PassArgs& a, cudaStream_t s);
 
 }  // namespace sfac

@@ -85,12 +85,30 @@ __device__ __forceinline__ void apply_spectral(C2<R> (&x)[E], int t, const C2<R>
     line_fft<R, N, E, true>(x, t, tw, ex);
 }
 
+// Zero the values at positions >= nmem (the padding of a zero-padded pass).
+template <typename R, int N, int E>
+__device__ __forceinline__ void zero_tail(C2<R> (&x)[E], int t, int nmem) {
+    constexpr int T = N / E;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (t + e * T >= nmem) x[e] = {R(0), R(0)};
+}
+
 // e^{tau/2 C} e^{tau S} e^{tau/2 C} on the line held in x (FP64 passes; the
-// tables hold e^{t lambda} / N).
-template <typename R, int N, int E, class Ex>
+// tables hold e^{t lambda} / N). PADDED: three zero-padded linear convolutions
+// with real multipliers, no twist.
+template <typename R, int N, int E, bool PADDED, class Ex>
 __device__ __forceinline__ void two_level_chain(C2<R> (&x)[E], int t, const PassArgs& a, const Ex& ex) {
     constexpr int T = N / E;
     const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
+    if constexpr (PADDED) {
+        apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eC));
+        zero_tail<R, N, E>(x, t, a.nmem);
+        apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eS));
+        zero_tail<R, N, E>(x, t, a.nmem);
+        apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eC));
+        return;
+    }
     const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
     // e^{tau/2 C}
     apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eC));
@@ -113,7 +131,9 @@ __device__ __forceinline__ void two_level_chain(C2<R> (&x)[E], int t, const Pass
 // and the result x0 + d is rounded once. Each increment is small against x0,
 // so its FP32 rounding is too, and the field itself is rounded once per pass
 // instead of after every factor. The tables hold expm1(t lambda) / N.
-template <typename R, int N, int E, class Ex>
+// PADDED: the three factors are zero-padded linear convolutions (no twist) and
+// the padding of each increment is zeroed before it is added.
+template <typename R, int N, int E, bool PADDED, class Ex>
 __device__ __forceinline__ void two_level_pass_incr(C2<R> (&x0)[E], int t, const PassArgs& a, const Ex& ex) {
     constexpr int T = N / E;
     const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
@@ -134,18 +154,29 @@ __device__ __forceinline__ void two_level_pass_incr(C2<R> (&x0)[E], int t, const
 #pragma unroll
     for (int e = 0; e < E; ++e) y[e] = cadd(x0[e], d[e]);
     apply_spectral<R, N, E>(y, t, tw, ex, eC);
+    if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
     for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
     // e^{tau S}
+    if constexpr (PADDED) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) y[e] = cmul(cadd(x0[e], d[e]), ldg_c2(twist + t + e * T));
-    apply_spectral<R, N, E>(y, t, tw, ex, eS);
+        for (int e = 0; e < E; ++e) y[e] = cadd(x0[e], d[e]);
+        apply_spectral<R, N, E>(y, t, tw, ex, eS);
+        zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
-    for (int e = 0; e < E; ++e) d[e] = cadd(d[e], cmulc(y[e], ldg_c2(twist + t + e * T)));
+        for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) y[e] = cmul(cadd(x0[e], d[e]), ldg_c2(twist + t + e * T));
+        apply_spectral<R, N, E>(y, t, tw, ex, eS);
+#pragma unroll
+        for (int e = 0; e < E; ++e) d[e] = cadd(d[e], cmulc(y[e], ldg_c2(twist + t + e * T)));
+    }
     // e^{tau/2 C}
 #pragma unroll
     for (int e = 0; e < E; ++e) y[e] = cadd(x0[e], d[e]);
     apply_spectral<R, N, E>(y, t, tw, ex, eC);
+    if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
     for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
     if (a.jq_out) {
@@ -162,20 +193,17 @@ __device__ __forceinline__ void two_level_pass_incr(C2<R> (&x0)[E], int t, const
 }
 
 // One whole pass on the line held in x: FP32 in increment form, FP64 plain.
-template <typename R, int N, int E, class Ex>
+template <typename R, int N, int E, bool PADDED, class Ex>
 __device__ __forceinline__ void fused_pass(C2<R> (&x)[E], int t, const PassArgs& a, const Ex& ex) {
     if constexpr (sizeof(R) == 4) {
-        two_level_pass_incr<R, N, E>(x, t, a, ex);
+        two_level_pass_incr<R, N, E, PADDED>(x, t, a, ex);
     } else {
         if (a.jq_in) jq_all<R, E>(x, a.jq_in_E, a.jq_in_1mE);
-        two_level_chain<R, N, E>(x, t, a, ex);
+        two_level_chain<R, N, E, PADDED>(x, t, a, ex);
         if (a.jq_out) jq_all<R, E>(x, a.jq_out_E, a.jq_out_1mE);
     }
 }
 
-// Global addressing of complex line `cl` (see PassArgs): element idx of the
-// line is (p0[idx], p1[idx]) for a contiguous pass and the 2-vector at
-// p0 + idx * stride for a strided pass.
 // Field loads: plain (may be served by L1) or .cg (L2 only). A persistent kernel
 // that reads data another SM wrote during the same launch uses .cg.
 template <bool CG, typename T>
@@ -184,28 +212,38 @@ __device__ __forceinline__ T ld_field(const T* p) {
     else return *p;
 }
 
-template <typename R, int N, bool STRIDED>
+// Global addressing of complex line `cl` (see PassArgs): element idx of the
+// line is (p0[idx], p1[idx]) for a contiguous pass and the 2-vector at
+// p0 + idx * stride for a strided pass. PADDED: lines hold nmem < N values
+// (loads beyond them give zeros, stores stop there) and a strided pass with an
+// odd inner extent moves its two columns as scalars (the second may not exist).
+template <typename R, int N, bool STRIDED, bool PADDED = false>
 struct LineRef {
     R* p0;
     R* p1;
     long long stride;
+    int nmem;
     bool active;
+    bool vec;  // strided pass moved as aligned 2-vectors
 
     __device__ __forceinline__ LineRef(const PassArgs& a, long long cl) {
         R* u = static_cast<R*>(a.u);
         active = cl < a.clines;
+        nmem = PADDED ? a.nmem : N;
         if (STRIDED) {
-            const long long pairs = a.inner >> 1;
+            const long long pairs = (a.inner + 1) >> 1;
             const long long o = active ? cl / pairs : 0;
             const long long c = active ? cl - o * pairs : 0;
-            p0 = u + o * (long long)N * a.inner + 2 * c;
-            p1 = nullptr;
+            p0 = u + o * (long long)nmem * a.inner + 2 * c;
+            vec = !PADDED || (a.inner & 1) == 0;
+            p1 = (active && 2 * c + 1 < a.inner) ? p0 + 1 : nullptr;
             stride = a.inner;
         } else {
             const long long r0 = active ? 2 * cl : 0;
-            p0 = u + r0 * N;
-            p1 = (active && r0 + 1 < a.outer) ? p0 + N : nullptr;
+            p0 = u + r0 * nmem;
+            p1 = (active && r0 + 1 < a.outer) ? p0 + nmem : nullptr;
             stride = 1;
+            vec = false;
         }
     }
 
@@ -218,9 +256,12 @@ struct LineRef {
             const long long step = T * stride;
 #pragma unroll
             for (int e = 0; e < E; ++e, q += step) {
-                if (active) {
+                const bool in = active && (!PADDED || t + e * T < nmem);
+                if (in && (!PADDED || vec)) {
                     const V v = ld_field<CG>(reinterpret_cast<const V*>(q));
                     x[e] = {v.x, v.y};
+                } else if (in) {
+                    x[e] = {ld_field<CG>(q), p1 ? ld_field<CG>(q + 1) : R(0)};
                 } else {
                     x[e] = {R(0), R(0)};
                 }
@@ -229,8 +270,9 @@ struct LineRef {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int idx = t + e * T;
-                x[e].x = active ? ld_field<CG>(p0 + idx) : R(0);
-                x[e].y = p1 ? ld_field<CG>(p1 + idx) : R(0);
+                const bool in = !PADDED || idx < nmem;
+                x[e].x = (active && in) ? ld_field<CG>(p0 + idx) : R(0);
+                x[e].y = (p1 && in) ? ld_field<CG>(p1 + idx) : R(0);
             }
         }
     }
@@ -245,15 +287,22 @@ struct LineRef {
             const long long step = T * stride;
 #pragma unroll
             for (int e = 0; e < E; ++e, q += step) {
-                V v;
-                v.x = x[e].x;
-                v.y = x[e].y;
-                *reinterpret_cast<V*>(q) = v;
+                if (PADDED && t + e * T >= nmem) continue;
+                if (!PADDED || vec) {
+                    V v;
+                    v.x = x[e].x;
+                    v.y = x[e].y;
+                    *reinterpret_cast<V*>(q) = v;
+                } else {
+                    q[0] = x[e].x;
+                    if (p1) q[1] = x[e].y;
+                }
             }
         } else {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int idx = t + e * T;
+                if (PADDED && idx >= nmem) continue;
                 p0[idx] = x[e].x;
                 if (p1) p1[idx] = x[e].y;
             }
@@ -283,7 +332,7 @@ struct PadExchange {
 };
 
 // MINB: minimum resident CTAs per SM the register allocation must allow.
-template <typename R, int N, int E, int LPC, bool STRIDED, int MINB>
+template <typename R, int N, int E, int LPC, bool STRIDED, int MINB, bool PADDED>
 __global__ void __launch_bounds__(LPC*(N / E), MINB)
 axis_pass_kernel(const PassArgs a) {
     constexpr int T = N / E;
@@ -295,12 +344,12 @@ axis_pass_kernel(const PassArgs a) {
     // contiguous passes: lanes walk along a line.
     const int j = STRIDED ? (tid % LPC) : (tid / T);
     const int t = STRIDED ? (tid / LPC) : (tid % T);
-    const LineRef<R, N, STRIDED> line(a, (long long)blockIdx.x * LPC + j);
+    const LineRef<R, N, STRIDED, PADDED> line(a, (long long)blockIdx.x * LPC + j);
     const Ex ex{reinterpret_cast<C2<R>*>(smem_raw), j};
 
     C2<R> x[E];
     line.template load<E>(x, t);
-    fused_pass<R, N, E>(x, t, a, ex);
+    fused_pass<R, N, E, PADDED>(x, t, a, ex);
     line.template store<E>(x, t);
 }
 
@@ -324,28 +373,28 @@ struct WarpExchange {
 
 // Lines [first, first + 32/T) of the pass `a`, processed by one warp. `region`
 // is this warp's shared memory: (32/T) * (N + N/E) complex values.
-template <typename R, int N, int E, bool STRIDED, bool CG>
+template <typename R, int N, int E, bool STRIDED, bool CG, bool PADDED = false>
 __device__ __forceinline__ void warp_pass_lines(const PassArgs& a, long long first, C2<R>* region, int lane) {
     constexpr int T = N / E;
     static_assert(T >= 1 && T <= 32, "line must fit one warp");
     using Ex = WarpExchange<R, N, E>;
     const int j = lane / T, t = lane % T;
-    const LineRef<R, N, STRIDED> line(a, first + j);
+    const LineRef<R, N, STRIDED, PADDED> line(a, first + j);
     const Ex ex{region + j * Ex::LINE_ELEMS};
     C2<R> x[E];
     line.template load<E, CG>(x, t);
-    fused_pass<R, N, E>(x, t, a, ex);
+    fused_pass<R, N, E, PADDED>(x, t, a, ex);
     line.template store<E>(x, t);
 }
 
-template <typename R, int N, int E, int WPB, bool STRIDED>
+template <typename R, int N, int E, int WPB, bool STRIDED, bool PADDED>
 __global__ void __launch_bounds__(WPB * 32)
 axis_pass_warp_kernel(const PassArgs a) {
     constexpr int LPW = 32 / (N / E);  // lines per warp
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     C2<R>* region = reinterpret_cast<C2<R>*>(smem_raw) + warp * LPW * WarpExchange<R, N, E>::LINE_ELEMS;
-    warp_pass_lines<R, N, E, STRIDED, false>(a, ((long long)blockIdx.x * WPB + warp) * LPW, region, lane);
+    warp_pass_lines<R, N, E, STRIDED, false, PADDED>(a, ((long long)blockIdx.x * WPB + warp) * LPW, region, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -366,7 +415,7 @@ cudaError_t set_smem(K kern, size_t smem, bool& configured) {
     return err;
 }
 
-template <typename R, int N, int E, int LPC, bool STRIDED>
+template <typename R, int N, int E, int LPC, bool STRIDED, bool PADDED>
 cudaError_t launch_cfg(const PassArgs& a, cudaStream_t s) {
     constexpr int T = N / E;
     // FP64 with 128-thread CTAs: at least two CTAs per SM, so one CTA's
@@ -374,7 +423,7 @@ cudaError_t launch_cfg(const PassArgs& a, cudaStream_t s) {
     constexpr int MINB = (sizeof(R) == 8 && LPC * T == 128) ? 2 : 1;
     using Ex = PadExchange<R, N, LPC, STRIDED>;
     const size_t smem = sizeof(C2<R>) * (size_t)Ex::elems();
-    auto kern = axis_pass_kernel<R, N, E, LPC, STRIDED, MINB>;
+    auto kern = axis_pass_kernel<R, N, E, LPC, STRIDED, MINB, PADDED>;
     static bool configured = false;
     cudaError_t err = set_smem(kern, smem, configured);
     if (err != cudaSuccess) return err;
@@ -385,11 +434,11 @@ cudaError_t launch_cfg(const PassArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <typename R, int N, int E, int WPB, bool STRIDED>
+template <typename R, int N, int E, int WPB, bool STRIDED, bool PADDED>
 cudaError_t launch_warp(const PassArgs& a, cudaStream_t s) {
     constexpr int LPC = WPB * (32 / (N / E));
     const size_t smem = sizeof(C2<R>) * (size_t)LPC * WarpExchange<R, N, E>::LINE_ELEMS;
-    auto kern = axis_pass_warp_kernel<R, N, E, WPB, STRIDED>;
+    auto kern = axis_pass_warp_kernel<R, N, E, WPB, STRIDED, PADDED>;
     static bool configured = false;
     cudaError_t err = set_smem(kern, smem, configured);
     if (err != cudaSuccess) return err;
@@ -400,7 +449,7 @@ cudaError_t launch_warp(const PassArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <typename R, int N>
+template <typename R, int N, bool PADDED>
 cudaError_t launch_n(const PassArgs& a, cudaStream_t s) {
     constexpr int E = elems_per_thread<N>();
     constexpr int T = N / E;
@@ -409,13 +458,13 @@ cudaError_t launch_n(const PassArgs& a, cudaStream_t s) {
         // for long lines (few lines: many small CTAs spread better over 152
         // SMs), four otherwise.
         constexpr int WPB = N >= 512 ? 2 : 4;
-        if (a.inner > 1) return launch_warp<R, N, 16, WPB, true>(a, s);
-        return launch_warp<R, N, 16, WPB, false>(a, s);
+        if (a.inner > 1) return launch_warp<R, N, 16, WPB, true, PADDED>(a, s);
+        return launch_warp<R, N, 16, WPB, false, PADDED>(a, s);
     } else if constexpr (sizeof(R) == 4 && N >= 1024) {
         // FP32, long lines: 16 values per thread and one line per CTA (64 to
         // 256 threads), which keeps the increment form's two arrays in registers.
-        if (a.inner > 1) return launch_cfg<R, N, 16, 1, true>(a, s);
-        return launch_cfg<R, N, 16, 1, false>(a, s);
+        if (a.inner > 1) return launch_cfg<R, N, 16, 1, true, PADDED>(a, s);
+        return launch_cfg<R, N, 16, 1, false, PADDED>(a, s);
     } else {
         // FP64 passes are bound by the FP64 pipe, not by memory: they take
         // 128-thread CTAs (several per SM, so one CTA's exchanges overlap
@@ -425,25 +474,25 @@ cudaError_t launch_n(const PassArgs& a, cudaStream_t s) {
         constexpr int MIN_S = (T >= 256 || sizeof(R) == 8) ? 1 : 32 / (2 * (int)sizeof(R));
         constexpr int LPC_S = (TPB / T) > MIN_S ? (TPB / T) : MIN_S;
         constexpr int LPC_C = (TPB / T) > 1 ? (TPB / T) : 1;
-        if (a.inner > 1) return launch_cfg<R, N, E, LPC_S, true>(a, s);
-        return launch_cfg<R, N, E, LPC_C, false>(a, s);
+        if (a.inner > 1) return launch_cfg<R, N, E, LPC_S, true, PADDED>(a, s);
+        return launch_cfg<R, N, E, LPC_C, false, PADDED>(a, s);
     }
 }
 
-template <typename R>
+template <typename R, bool PADDED>
 cudaError_t launch_pass_any(int N, const PassArgs& a, cudaStream_t s) {
     switch (N) {
-        case 4: return launch_n<R, 4>(a, s);
-        case 8: return launch_n<R, 8>(a, s);
-        case 16: return launch_n<R, 16>(a, s);
-        case 32: return launch_n<R, 32>(a, s);
-        case 64: return launch_n<R, 64>(a, s);
-        case 128: return launch_n<R, 128>(a, s);
-        case 256: return launch_n<R, 256>(a, s);
-        case 512: return launch_n<R, 512>(a, s);
-        case 1024: return launch_n<R, 1024>(a, s);
-        case 2048: return launch_n<R, 2048>(a, s);
-        case 4096: return launch_n<R, 4096>(a, s);
+        case 4: return launch_n<R, 4, PADDED>(a, s);
+        case 8: return launch_n<R, 8, PADDED>(a, s);
+        case 16: return launch_n<R, 16, PADDED>(a, s);
+        case 32: return launch_n<R, 32, PADDED>(a, s);
+        case 64: return launch_n<R, 64, PADDED>(a, s);
+        case 128: return launch_n<R, 128, PADDED>(a, s);
+        case 256: return launch_n<R, 256, PADDED>(a, s);
+        case 512: return launch_n<R, 512, PADDED>(a, s);
+        case 1024: return launch_n<R, 1024, PADDED>(a, s);
+        case 2048: return launch_n<R, 2048, PADDED>(a, s);
+        case 4096: return launch_n<R, 4096, PADDED>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -4,6 +4,6 @@
 
 namespace sfac {
 cudaError_t launch_pass_f32(int N, const PassArgs& a, cudaStream_t s) {
-    return launch_pass_any<float>(N, a, s);
+    return launch_pass_any<float, false>(N, a, s);
 }
 }  // namespace sfac

@@ -2,6 +2,7 @@
 // the per-axis tables, the device plan and the C ABI declared in sfac.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -10,6 +11,7 @@
 #include <vector>
 
 #include "sfac.h"
+#include "sfac_diag.h"
 #include "sfac_host.h"
 #include "sfac_internal.h"
 
@@ -50,8 +52,12 @@ sfac_status validate(const sfac_params* p, bool need_supported) {
     for (int l = 0; l < p->dim; ++l) {
         if (p->n[l] < 1) return fail(SFAC_EINVAL, "n[l] must be >= 1");
         if (!(p->alpha[l] > 1.0 && p->alpha[l] < 2.0)) return fail(SFAC_EINVAL, "alpha[l] must lie in (1, 2)");
-        if (need_supported && (!is_pow2(p->n[l]) || p->n[l] < 4 || p->n[l] > 4096))
-            return fail(SFAC_EUNSUPPORTED, "n[l] must be a power of two in [4, 4096]");
+        if (need_supported && p->n[l] < 2)
+            return fail(SFAC_EUNSUPPORTED, "n[l] must be at least 2");
+        if (need_supported && !(is_pow2(p->n[l]) && p->n[l] >= 4) && p->n[l] > 2048)
+            return fail(SFAC_EUNSUPPORTED, "n[l] must be a power of two <= 4096 or any length <= 2048");
+        if (need_supported && is_pow2(p->n[l]) && p->n[l] > 4096)
+            return fail(SFAC_EUNSUPPORTED, "n[l] must be a power of two <= 4096 or any length <= 2048");
         pts *= p->n[l];
     }
     if (pts > (1LL << 34)) return fail(SFAC_EUNSUPPORTED, "grid too large");
@@ -72,7 +78,17 @@ struct sfac_plan {
         const void* eS;
         const void* twist;
         const void* twid;
+        int fft_len;  // N of the pass: n, or the padded length L
+        bool padded;
+        // FP64 diagnostic tables: lambda/N, mu/N, twist, twiddles (padded axes:
+        // the multiplier of B, -, -, twiddles)
+        const double* dA;
+        const double* dB;
+        const void* dtwist;
+        const void* dtwid;
     } ax[3] = {};
+    double3* diag_partial = nullptr;
+    double* diag_out = nullptr;
     double jq_half_E = 0, jq_half_1mE = 0, jq_full_E = 0, jq_full_1mE = 0;
     void* staging = nullptr;
 };
@@ -98,12 +114,14 @@ struct DeviceGuard {
 sfac_status launch_axis(sfac_plan* P, void* u, int ax, int jq_in, int jq_out, cudaStream_t st) {
     long long inner = 1;
     for (int l = 0; l < ax; ++l) inner *= P->p.n[l];
-    const int N = P->p.n[ax];
+    const int n = P->p.n[ax];
+    const int N = P->ax[ax].fft_len;
     sfac::PassArgs a;
     a.u = u;
     a.inner = inner;
-    a.outer = P->npts / ((long long)N * inner);
-    a.clines = (ax == 0) ? (a.outer + 1) / 2 : a.outer * (inner / 2);
+    a.outer = P->npts / ((long long)n * inner);
+    a.clines = (ax == 0) ? (a.outer + 1) / 2 : a.outer * ((inner + 1) / 2);
+    a.nmem = n;
     a.eC = P->ax[ax].eC;
     a.eS = P->ax[ax].eS;
     a.twist = P->ax[ax].twist;
@@ -114,8 +132,11 @@ sfac_status launch_axis(sfac_plan* P, void* u, int ax, int jq_in, int jq_out, cu
     a.jq_out = jq_out != 0;
     a.jq_out_E = jq_out == 2 ? P->jq_full_E : P->jq_half_E;
     a.jq_out_1mE = jq_out == 2 ? P->jq_full_1mE : P->jq_half_1mE;
-    const cudaError_t err = (P->p.prec == SFAC_FP64) ? sfac::launch_pass_f64(N, a, st)
-                                                     : sfac::launch_pass_f32(N, a, st);
+    cudaError_t err;
+    if (P->ax[ax].padded)
+        err = (P->p.prec == SFAC_FP64) ? sfac::launch_pass_padded_f64(N, a, st) : sfac::launch_pass_padded_f32(N, a, st);
+    else
+        err = (P->p.prec == SFAC_FP64) ? sfac::launch_pass_f64(N, a, st) : sfac::launch_pass_f32(N, a, st);
     if (err != cudaSuccess) return cuda_fail(err, "axis pass launch");
     return SFAC_OK;
 }
@@ -185,9 +206,19 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
     P->jq_full_1mE = -std::expm1(-2.0 * params->tau);
 
     AxisHost host[3];
+    sfac::AxisPadded pad[3];
+    bool padded[3] = {false, false, false};
     try {
-        for (int l = 0; l < params->dim; ++l)
+        long long inner = 1;
+        for (int l = 0; l < params->dim; ++l) {
             compute_axis(params->alpha[l], params->eps, params->tau, params->a, params->b, params->n[l], &host[l]);
+            // Zero-padded pass for lengths that are not powers of two >= 4, and for
+            // any strided axis (l > 0) whose stride (the product of the earlier
+            // extents) is odd: its column pairs are not 2-vector aligned.
+            padded[l] = !(is_pow2(params->n[l]) && params->n[l] >= 4) || (l > 0 && (inner & 1));
+            if (padded[l]) sfac::compute_axis_padded(host[l], params->tau, &pad[l]);
+            inner *= params->n[l];
+        }
     } catch (const std::bad_alloc&) {
         delete P;
         return fail(SFAC_ENOMEM, "host allocation failed");
@@ -199,15 +230,28 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
     }
     // One device block: per axis eC[n], eS[n], twist[2n], twid[2n] reals.
     const size_t rs = real_size(P);
-    size_t off[3][4], total = 0;
-    for (int l = 0; l < params->dim; ++l) {
-        const size_t n = (size_t)params->n[l];
-        const size_t sz[4] = {n * rs, n * rs, 2 * n * rs, 2 * n * rs};
-        for (int q = 0; q < 4; ++q) {
-            off[l][q] = total;
-            total += align256(sz[q]);
+    size_t off[3][8], total = 0;
+    long long max_partials = 1;
+    {
+        long long inner = 1;
+        for (int l = 0; l < params->dim; ++l) {
+            const size_t n = padded[l] ? (size_t)pad[l].L : (size_t)params->n[l];
+            const size_t sz[8] = {n * rs, n * rs, padded[l] ? 0 : 2 * n * rs, 2 * n * rs,
+                                  n * 8,  padded[l] ? 0 : n * 8, padded[l] ? 0 : 2 * n * 8, 2 * n * 8};
+            for (int q = 0; q < 8; ++q) {
+                off[l][q] = total;
+                total += align256(sz[q]);
+            }
+            const long long outer = P->npts / ((long long)params->n[l] * inner);
+            const long long clines = l == 0 ? (outer + 1) / 2 : outer * ((inner + 1) / 2);
+            max_partials = std::max(max_partials, sfac::diag_partials_needed(clines, (int)n));
+            inner *= params->n[l];
         }
     }
+    const size_t off_partial = total;
+    total += align256(sizeof(double3) * (size_t)max_partials);
+    const size_t off_out = total;
+    total += align256(4 * sizeof(double));
     std::vector<unsigned char> blob;
     try {
         blob.assign(total, 0);
@@ -217,8 +261,32 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
     }
     for (int l = 0; l < params->dim; ++l) {
         const bool f64 = params->prec == SFAC_FP64;
+        const std::vector<double> none;
         const std::vector<double>* src[4] = {f64 ? &host[l].eC : &host[l].dC, f64 ? &host[l].eS : &host[l].dS,
                                              &host[l].twist, &host[l].twid};
+        if (padded[l]) {
+            src[0] = f64 ? &pad[l].mC : &pad[l].mC1;
+            src[1] = f64 ? &pad[l].mS : &pad[l].mS1;
+            src[2] = &none;
+            src[3] = &pad[l].twid;
+        }
+        // FP64 diagnostic tables
+        std::vector<double> lamN, muN;
+        if (!padded[l]) {
+            const double inv = 1.0 / (double)params->n[l];
+            lamN.resize(params->n[l]);
+            muN.resize(params->n[l]);
+            for (int j = 0; j < params->n[l]; ++j) {
+                lamN[j] = host[l].lambda[j] * inv;
+                muN[j] = host[l].mu[j] * inv;
+            }
+        }
+        const std::vector<double>* dsrc[4] = {padded[l] ? &pad[l].mB : &lamN, padded[l] ? &none : &muN,
+                                              padded[l] ? &none : &host[l].twist,
+                                              padded[l] ? &pad[l].twid : &host[l].twid};
+        for (int q = 0; q < 4; ++q)
+            if (!dsrc[q]->empty())
+                std::memcpy(blob.data() + off[l][4 + q], dsrc[q]->data(), dsrc[q]->size() * sizeof(double));
         for (int q = 0; q < 4; ++q) {
             unsigned char* dst = blob.data() + off[l][q];
             const std::vector<double>& v = *src[q];
@@ -248,9 +316,17 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
     for (int l = 0; l < params->dim; ++l) {
         P->ax[l].eC = base + off[l][0];
         P->ax[l].eS = base + off[l][1];
-        P->ax[l].twist = base + off[l][2];
+        P->ax[l].twist = padded[l] ? nullptr : base + off[l][2];
         P->ax[l].twid = base + off[l][3];
+        P->ax[l].padded = padded[l];
+        P->ax[l].fft_len = padded[l] ? pad[l].L : params->n[l];
+        P->ax[l].dA = reinterpret_cast<const double*>(base + off[l][4]);
+        P->ax[l].dB = padded[l] ? nullptr : reinterpret_cast<const double*>(base + off[l][5]);
+        P->ax[l].dtwist = padded[l] ? nullptr : base + off[l][6];
+        P->ax[l].dtwid = base + off[l][7];
     }
+    P->diag_partial = reinterpret_cast<double3*>(base + off_partial);
+    P->diag_out = reinterpret_cast<double*>(base + off_out);
     *out = P;
     return SFAC_OK;
 }
@@ -289,6 +365,52 @@ sfac_status sfac_axis_pass(sfac_plan* plan, void* u_dev, int axis, int jq_in, in
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
     return launch_axis(plan, u_dev, axis, jq_in, jq_out, static_cast<cudaStream_t>(stream));
+}
+
+sfac_status sfac_plan_info(const sfac_plan* plan, int axis, int* fft_len, int* padded) {
+    if (!plan || axis < 0 || axis >= plan->p.dim) return fail(SFAC_EINVAL, "bad plan or axis");
+    if (fft_len) *fft_len = plan->ax[axis].fft_len;
+    if (padded) *padded = plan->ax[axis].padded ? 1 : 0;
+    return SFAC_OK;
+}
+
+sfac_status sfac_diagnostics(sfac_plan* plan, const void* u_dev, double* out, void* stream) {
+    if (!plan || !u_dev || !out) return fail(SFAC_EINVAL, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(u_dev) % 16 != 0) return fail(SFAC_EINVAL, "u_dev must be 16-byte aligned");
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t err = cudaMemsetAsync(plan->diag_out, 0, 3 * sizeof(double), st);
+    if (err != cudaSuccess) return cuda_fail(err, "diagnostics reset");
+    long long inner = 1;
+    double hprod = 1.0;
+    for (int ax = 0; ax < plan->p.dim; ++ax) {
+        const int n = plan->p.n[ax];
+        sfac::PassArgs a;
+        a.u = const_cast<void*>(u_dev);
+        a.inner = inner;
+        a.outer = plan->npts / ((long long)n * inner);
+        a.clines = (ax == 0) ? (a.outer + 1) / 2 : a.outer * ((inner + 1) / 2);
+        a.nmem = n;
+        a.eC = a.eS = nullptr;
+        a.twist = plan->ax[ax].dtwist;
+        a.twid = plan->ax[ax].dtwid;
+        a.jq_in = a.jq_out = 0;
+        a.jq_in_E = a.jq_in_1mE = a.jq_out_E = a.jq_out_1mE = 0.0;
+        err = sfac::launch_diag_axis(plan->p.prec == SFAC_FP64, plan->ax[ax].padded, plan->ax[ax].fft_len, a,
+                                     plan->ax[ax].dA, plan->ax[ax].dB, ax == 0, plan->diag_partial,
+                                     plan->diag_out, st);
+        if (err != cudaSuccess) return cuda_fail(err, "diagnostics launch");
+        inner *= n;
+        hprod *= (plan->p.b - plan->p.a) / (double)(n + 1);
+    }
+    double host[3];
+    err = cudaMemcpyAsync(host, plan->diag_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return cuda_fail(err, "diagnostics copy");
+    out[0] = host[2];                                 // max |u|
+    out[1] = hprod * (0.25 * host[1] - 0.5 * host[0]);  // discrete energy
+    return SFAC_OK;
 }
 
 sfac_status sfac_solve(sfac_plan* plan, void* u_dev, double T, void* stream) {

@@ -58,6 +58,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sfac_solve": (ctypes.c_int, [vp, vp, d, vp]),
         "sfac_step_host": (ctypes.c_int, [vp, vp, ll, vp]),
         "sfac_axis_pass": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]),
+        "sfac_diagnostics": (ctypes.c_int, [vp, vp, P(d), vp]),
+        "sfac_plan_info": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]),
         "sfac_plan_tables": (ctypes.c_int, [P(SfacParams), ctypes.c_int, P(d), P(d), P(d), P(d)]),
         "sfac_batch_create": (ctypes.c_int, [P(SfacParams), ctypes.c_int, vp, P(vp)]),
         "sfac_batch_destroy": (ctypes.c_int, [vp]),
@@ -165,6 +167,20 @@ def sfac_step_host(plan: int, u_host, nsteps: int, stream=None) -> None:
 def sfac_axis_pass(plan: int, u, axis: int, jq_in: int = 0, jq_out: int = 0, stream=None) -> None:
     _check(load().sfac_axis_pass(plan, _ptr(u), int(axis), int(jq_in), int(jq_out), _stream(stream)),
            "sfac_axis_pass")
+
+
+def sfac_plan_info(plan: int, axis: int):
+    """(FFT length, padded?) of the plan's pass along `axis`."""
+    L, pad = ctypes.c_int(), ctypes.c_int()
+    _check(load().sfac_plan_info(plan, int(axis), ctypes.byref(L), ctypes.byref(pad)), "sfac_plan_info")
+    return L.value, bool(pad.value)
+
+
+def sfac_diagnostics(plan: int, u, stream=None):
+    """(max |u|, discrete energy) of the field u (Examples 4 and 5)."""
+    out = (ctypes.c_double * 2)()
+    _check(load().sfac_diagnostics(plan, _ptr(u), out, _stream(stream)), "sfac_diagnostics")
+    return out[0], out[1]
 
 
 def sfac_plan_tables(params: SfacParams, axis: int):
@@ -437,6 +453,11 @@ class Plan:
         self._check_field(u)
         sfac_axis_pass(self.handle, u, axis, jq_in, jq_out, stream)
         return u
+
+    def diagnostics(self, u, stream=None):
+        """(max |u|, discrete energy E(u)) of a field of this plan."""
+        self._check_field(u)
+        return sfac_diagnostics(self.handle, u, stream)
 
     def step_host(self, u_host, nsteps: int, stream=None):
         sfac_step_host(self.handle, u_host, nsteps, stream)

@@ -48,7 +48,8 @@ def test_version(lib):
     (dict(n=(64, 64), alpha=(1.5, 1.5), eps=0.1, tau=-1.0), S.sfac.SFAC_EINVAL),
     (dict(n=(64, 64), alpha=(1.5, 1.5), eps=0.1, tau=0.01, a=1.0, b=1.0), S.sfac.SFAC_EINVAL),
     (dict(n=(64, 0), alpha=(1.5, 1.5), eps=0.1, tau=0.01), S.sfac.SFAC_EINVAL),
-    (dict(n=(63, 64), alpha=(1.5, 1.5), eps=0.1, tau=0.01), S.sfac.SFAC_EUNSUPPORTED),
+    (dict(n=(3000, 64), alpha=(1.5, 1.5), eps=0.1, tau=0.01), S.sfac.SFAC_EUNSUPPORTED),
+    (dict(n=(1, 64), alpha=(1.5, 1.5), eps=0.1, tau=0.01), S.sfac.SFAC_EUNSUPPORTED),
     (dict(n=(8192, 64), alpha=(1.5, 1.5), eps=0.1, tau=0.01), S.sfac.SFAC_EUNSUPPORTED),
 ])
 def test_plan_create_rejects_on_host(lib, kw, status):

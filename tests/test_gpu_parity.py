@@ -223,3 +223,104 @@ def test_fp32_error_against_fp64_oracle(which):
     err = float(np.abs(got - ref).max())
     print(f"{which}: FP32 max-norm error {err:.3e}")
     assert err <= 1e-5
+
+
+# ---- lengths that are not powers of two (zero-padded convolution passes) -------
+
+ODD_SHAPES = [(63,), (2,), (3, 5), (100, 30), (63, 63), (64, 63), (63, 64), (255, 8), (7, 9, 11), (63, 16, 17),
+              (1000, 3), (2048, 2)]
+
+
+@pytest.mark.parametrize("n", ODD_SHAPES, ids=str)
+def test_padded_axis_pass_equals_dense_factor(n):
+    prob = I.Problem(n=n, alpha=(1.3, 1.7, 1.5)[: len(n)], eps=0.1, tau=0.02)
+    u0 = I.random_field(prob, 13, -1.0, 1.0)
+    sch = O.Scheme.for_problem(prob)
+    with S.Plan.for_problem(prob) as plan:
+        for ax in range(len(n)):
+            u = to_dev(u0, S.SFAC_FP64)
+            plan.axis_pass(u, ax, 0, 0)
+            torch.cuda.synchronize()
+            ref = O.apply_axis(u0, sch.P[ax], ax + 1)
+            assert rel_err(u.cpu().numpy(), ref) <= TOL64, (n, ax)
+
+
+@pytest.mark.parametrize("n", [(63, 63), (31, 64, 5), (255, 100)], ids=str)
+@pytest.mark.parametrize("prec", [S.SFAC_FP64, S.SFAC_FP32])
+def test_padded_steps_match_oracle(n, prec):
+    prob = I.Problem(n=n, alpha=(1.25, 1.75, 1.5)[: len(n)], eps=0.07, tau=0.01)
+    u0 = I.random_field(prob, 14)
+    ref = O.Scheme.for_problem(prob).run(u0, 12)
+    if prec == S.SFAC_FP64:
+        assert rel_err(gpu_run(prob, u0, 12), ref) <= TOL64
+    else:
+        u32 = np.asarray(u0, np.float32).astype(np.float64)
+        assert np.abs(gpu_run(prob, u32, 12, S.SFAC_FP32) - ref).max() <= 1e-5
+
+
+def _close_to_printed(value, printed):
+    unit = 10.0 ** (np.floor(np.log10(printed)) - 4)
+    return abs(value - printed) <= unit + 2e-13
+
+
+@pytest.mark.parametrize("row", [(1.2, 1.4, 100, 1.2824e-7), (1.5, 1.5, 100, 3.8688e-7),
+                                 (1.6, 1.9, 100, 4.0334e-6), (1.2, 1.8, 200, 8.3546e-7)],
+                         ids=lambda r: f"{r[:3]}")
+def test_table2_example1_on_gpu(row):
+    """Table 2 (Example 1, n = 255 on (0,2)^2) reproduced by the FP64 device path:
+    E_t = max|u(tau) - u(tau/2)| at T = 1 to the printed digits."""
+    a1, a2, ninv, printed = row
+    res = []
+    for N in (ninv, 2 * ninv):
+        p = I.example1_problem((a1, a2), 1.0 / N)
+        res.append(gpu_run(p, I.example1_u0(p), N))
+    et = float(np.abs(res[0] - res[1]).max())
+    print(f"Table 2 {row[:3]}: GPU E_t {et:.5e} printed {printed:.4e}")
+    assert _close_to_printed(et, printed)
+
+
+# ---- monitoring reductions (max|u| and the discrete energy, Examples 4-5) ------
+
+@pytest.mark.parametrize("n", [(64, 32), (63, 50), (16, 8, 32), (15, 7, 9), (1024, 4)], ids=str)
+@pytest.mark.parametrize("prec", [S.SFAC_FP64, S.SFAC_FP32])
+def test_diagnostics_match_oracle(n, prec):
+    prob = I.Problem(n=n, alpha=(1.3, 1.8, 1.5)[: len(n)], eps=0.05, tau=0.01)
+    u0 = I.random_field(prob, 15, -1.0, 1.0)
+    if prec == S.SFAC_FP32:
+        u0 = np.asarray(u0, np.float32).astype(np.float64)
+    sch = O.Scheme.for_problem(prob)
+    e_ref = O.discrete_energy(u0, sch)
+    with S.Plan.for_problem(prob, prec) as plan:
+        mx, en = plan.diagnostics(to_dev(u0, prec))
+    assert mx == pytest.approx(np.abs(u0).max(), rel=1e-15)
+    assert abs(en - e_ref) <= 1e-12 * max(1.0, abs(e_ref)), (en, e_ref)
+
+
+def test_energy_decays_example5():
+    """Example 5: on (0,1)^2 with h = 1/128, eps = 0.01, tau = 0.01 and
+    u0 = 0.8 rand - 0.4 the discrete energy decreases step after step."""
+    prob = I.Problem(n=(127, 127), alpha=(1.5, 1.7), eps=0.01, tau=0.01, a=0.0, b=1.0)
+    u0 = I.random_field(prob, 16, -0.4, 0.4)
+    with S.Plan.for_problem(prob) as plan:
+        u = to_dev(u0, S.SFAC_FP64)
+        energies, norms = [], []
+        for _ in range(40):
+            mx, en = plan.diagnostics(u)
+            energies.append(en)
+            norms.append(mx)
+            plan.step(u, 1)
+    assert all(b <= a + 1e-14 * abs(a) for a, b in zip(energies, energies[1:]))
+    assert max(norms) <= 1.0
+
+
+@pytest.mark.parametrize("n,expect", [
+    ((1024, 1024), [(1024, False), (1024, False)]),
+    ((256, 256, 256), [(256, False)] * 3),
+    ((63, 64), [(128, True), (128, True)]),      # odd stride sends axis 2 to the padded pass
+    ((64, 63), [(64, False), (128, True)]),
+    ((2, 8), [(4, True), (8, False)]),
+], ids=str)
+def test_pass_routing(n, expect):
+    prob = I.Problem(n=n, alpha=(1.5,) * len(n), eps=0.1, tau=0.01)
+    with S.Plan.for_problem(prob) as plan:
+        assert [S.sfac_plan_info(plan.handle, ax) for ax in range(len(n))] == expect
