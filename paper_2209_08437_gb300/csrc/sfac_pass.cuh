@@ -53,10 +53,13 @@ __device__ __forceinline__ R jq_increment(R v, R omE) {
     return v * q / (s * (R(1) + s));
 }
 
+// Table reads. Tables may sit in global memory or, in the persistent kernels,
+// in shared memory: plain loads serve both (the address space is inferred
+// where the pointer is known).
 template <typename R>
 __device__ __forceinline__ C2<R> ldg_c2(const C2<R>* p) {
     using V = typename Vec2T<R>::type;
-    const V v = __ldg(reinterpret_cast<const V*>(p));
+    const V v = *reinterpret_cast<const V*>(p);
     return {v.x, v.y};
 }
 
@@ -78,7 +81,7 @@ __device__ __forceinline__ void apply_spectral(C2<R> (&x)[E], int t, const C2<R>
     line_fft<R, N, E, false>(x, t, tw, ex);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const R s = __ldg(m + t + e * T);
+        const R s = m[t + e * T];
         x[e].x *= s;
         x[e].y *= s;
     }
@@ -387,14 +390,50 @@ __device__ __forceinline__ void warp_pass_lines(const PassArgs& a, long long fir
     line.template store<E>(x, t);
 }
 
+// Shared-memory tables of one axis for the persistent kernels: eC[N], eS[N],
+// twist[N] (not for padded passes) and twiddles[N], copied once per CTA.
+template <typename R, int N, bool PADDED>
+struct SmemTables {
+    static constexpr size_t BYTES = 2 * N * sizeof(R) + (PADDED ? 1 : 2) * N * sizeof(C2<R>);
+    static __device__ __forceinline__ void load(PassArgs& a, unsigned char* smem) {
+        R* eC = reinterpret_cast<R*>(smem);
+        R* eS = eC + N;
+        C2<R>* tw = reinterpret_cast<C2<R>*>(eS + N);
+        C2<R>* twist = tw + N;
+        const R* gC = static_cast<const R*>(a.eC);
+        const R* gS = static_cast<const R*>(a.eS);
+        const C2<R>* gtw = static_cast<const C2<R>*>(a.twid);
+        const C2<R>* gtwist = static_cast<const C2<R>*>(a.twist);
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            eC[i] = gC[i];
+            eS[i] = gS[i];
+            tw[i] = gtw[i];
+            if (!PADDED) twist[i] = gtwist[i];
+        }
+        __syncthreads();
+        a.eC = eC;
+        a.eS = eS;
+        a.twid = tw;
+        a.twist = PADDED ? nullptr : twist;
+    }
+};
+
+// Persistent: each CTA copies the axis tables to shared memory once, then its
+// warps take warp-groups of lines (32/T lines each) in a grid-stride loop.
 template <typename R, int N, int E, int WPB, bool STRIDED, bool PADDED>
 __global__ void __launch_bounds__(WPB * 32)
-axis_pass_warp_kernel(const PassArgs a) {
+axis_pass_warp_kernel(const PassArgs a0, long long ngroups) {
     constexpr int LPW = 32 / (N / E);  // lines per warp
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    PassArgs a = a0;
+    SmemTables<R, N, PADDED>::load(a, smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C2<R>* region = reinterpret_cast<C2<R>*>(smem_raw) + warp * LPW * WarpExchange<R, N, E>::LINE_ELEMS;
-    warp_pass_lines<R, N, E, STRIDED, false, PADDED>(a, ((long long)blockIdx.x * WPB + warp) * LPW, region, lane);
+    C2<R>* region = reinterpret_cast<C2<R>*>(smem_raw + SmemTables<R, N, PADDED>::BYTES) +
+                    warp * LPW * WarpExchange<R, N, E>::LINE_ELEMS;
+    for (long long g = (long long)blockIdx.x * WPB + warp; g < ngroups; g += (long long)gridDim.x * WPB) {
+        warp_pass_lines<R, N, E, STRIDED, false, PADDED>(a, g * LPW, region, lane);
+        __syncwarp();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -436,16 +475,27 @@ cudaError_t launch_cfg(const PassArgs& a, cudaStream_t s) {
 
 template <typename R, int N, int E, int WPB, bool STRIDED, bool PADDED>
 cudaError_t launch_warp(const PassArgs& a, cudaStream_t s) {
-    constexpr int LPC = WPB * (32 / (N / E));
-    const size_t smem = sizeof(C2<R>) * (size_t)LPC * WarpExchange<R, N, E>::LINE_ELEMS;
+    constexpr int LPW = 32 / (N / E);
+    const size_t smem = SmemTables<R, N, PADDED>::BYTES +
+                        sizeof(C2<R>) * (size_t)WPB * LPW * WarpExchange<R, N, E>::LINE_ELEMS;
     auto kern = axis_pass_warp_kernel<R, N, E, WPB, STRIDED, PADDED>;
     static bool configured = false;
+    static int resident = 0;  // CTAs per SM x SMs
     cudaError_t err = set_smem(kern, smem, configured);
     if (err != cudaSuccess) return err;
-    const long long grid = (a.clines + LPC - 1) / LPC;
-    if (grid <= 0) return cudaSuccess;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    kern<<<(unsigned)grid, WPB * 32, smem, s>>>(a);
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
+        if (err != cudaSuccess) return err;
+        resident = (per_sm < 1 ? 1 : per_sm) * (sms < 1 ? 1 : sms);
+    }
+    const long long ngroups = (a.clines + LPW - 1) / LPW;
+    if (ngroups <= 0) return cudaSuccess;
+    const long long want = (ngroups + WPB - 1) / WPB;
+    const long long grid = want < resident ? want : resident;
+    kern<<<(unsigned)grid, WPB * 32, smem, s>>>(a, ngroups);
     return cudaGetLastError();
 }
 
