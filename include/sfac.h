@@ -91,6 +91,30 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
  * convolution pass, 0 for the spectral pass with the twist. */
 sfac_status sfac_plan_info(const sfac_plan* plan, int axis, int* fft_len, int* padded);
 
+/* Kernels of an axis pass (sfac_plan_kernel). The paper has no counterpart;
+ * these describe only how libsfac maps the pass of Sec. 2.2 onto the GPU. */
+#define SFAC_KERNEL_CTA 0    /* lines spread over a CTA, CTA-wide exchanges (FP64; FP32 n >= 1024) */
+#define SFAC_KERNEL_WARP 1   /* FP32, 32 <= N <= 512: lines held inside one warp, persistent CTAs */
+#define SFAC_KERNEL_STAGED 2 /* the warp kernel fed by TMA tile copies (FP32 strided axes) */
+
+/* Which kernel a pass of axis `axis` would use for the field at u_dev: *kind
+ * receives one of SFAC_KERNEL_*. The staged kernel needs an FP32 plan, a
+ * spectral (not zero-padded) pass of length 32..512 on a strided axis (axis >= 1)
+ * whose stride, the product of the earlier extents, is a multiple of 4 and at
+ * least the tile width W (32 floats; 16 from length 256), at least as many
+ * tiles (W columns of one slab) as the device has SMs, and u_dev 16-byte
+ * aligned; otherwise the pass runs the warp or CTA kernel, with the same
+ * arithmetic. Host-only; nothing is enqueued. */
+sfac_status sfac_plan_kernel(const sfac_plan* plan, int axis, const void* u_dev, int* kind);
+
+/* Synchronise `stream`, then report whether an axis pass of this plan gave up
+ * on one of its bounded waits since the last check: SFAC_ETIMEOUT if so (the
+ * field written by that pass is not valid; the flag is cleared), SFAC_OK
+ * otherwise. Only the staged kernel waits (on its tile copies, about two
+ * seconds at most per wait); sfac_step_host checks automatically. The paper has
+ * no counterpart. */
+sfac_status sfac_plan_check(sfac_plan* plan, void* stream);
+
 /* Release a plan and its device memory. Synchronises the device first so that no
  * enqueued work still reads the tables. NULL is accepted (no-op). */
 sfac_status sfac_plan_destroy(sfac_plan* plan);

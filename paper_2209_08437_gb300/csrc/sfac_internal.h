@@ -41,7 +41,12 @@ struct PassArgs {
     double jq_in_E, jq_in_1mE;
     double jq_out_E, jq_out_1mE;
     int jq_in, jq_out;
+    // Device word where a kernel that gave up waiting for one of its own
+    // asynchronous copies records SFAC_PASS_TIMEOUT (NULL: not recorded).
+    unsigned int* status = nullptr;
 };
+
+constexpr unsigned int SFAC_PASS_TIMEOUT = 1u;
 
 // Launch one pass for line length N (a power of two in [4, 4096]).
 // Returns cudaErrorInvalidValue for an unsupported N.
@@ -55,5 +60,15 @@ cudaError_t launch_pass_f32(int N, const PassArgs& a, cudaStream_t s);
 // FFT, multiply, inverse FFT, zero the values past nmem.
 cudaError_t launch_pass_padded_f64(int N, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_pass_padded_f32(int N, const PassArgs& a, cudaStream_t s);
+
+// FP32 strided pass with TMA-staged tiles (sfac_pass_staged.cuh). Returns
+// cudaErrorNotSupported, having enqueued nothing, when the pass does not
+// qualify (see staged_pass_eligible); the caller then uses launch_pass_f32.
+cudaError_t launch_pass_staged_f32(int N, const PassArgs& a, cudaStream_t s);
+// Whether launch_pass_staged_f32 takes this pass: FP32 lines of a power-of-two
+// N in [32, 512] (not zero-padded), a strided axis with inner % 4 == 0 and
+// inner >= the tile width, at least one tile per SM, u 16-byte aligned, and the
+// driver's tensor-map encoder available.
+bool staged_pass_eligible(int N, const PassArgs& a);
 
 }  // namespace sfac

@@ -45,12 +45,15 @@ __device__ __forceinline__ R jq_flow(R v, R E, R omE) {
 
 // Increment of J^Q for the FP32 passes: with q = (1 - E)(1 - v)(1 + v) the
 // flow is v / sqrt(1 - q) = v + v q / (s (1 + s)), s = sqrt(1 - q); this returns
-// the added term v q / (s (1 + s)), which is small, so its rounding is too.
-template <typename R>
-__device__ __forceinline__ R jq_increment(R v, R omE) {
-    const R q = omE * (R(1) - v) * (R(1) + v);
-    const R s = sqrt(R(1) - q);
-    return v * q / (s * (R(1) + s));
+// the added term v q / (s (1 + s)) = v q r / (1 + s) with r = 1/s. The term is
+// about tau |v| at most, so the few-ulp reciprocal square root and fast divide
+// used here change the result by far less than the final rounding of x0 + d.
+// (1 - q >= E > 0, so both are in range.)
+__device__ __forceinline__ float jq_increment(float v, float omE) {
+    const float q = omE * (1.f - v) * (1.f + v);
+    const float r = rsqrtf(1.f - q);
+    const float s = (1.f - q) * r;
+    return __fdividef(v * q * r, 1.f + s);
 }
 
 // Table reads. Tables may sit in global memory or, in the persistent kernels,
@@ -136,26 +139,32 @@ __device__ __forceinline__ void two_level_chain(C2<R> (&x)[E], int t, const Pass
 // instead of after every factor. The tables hold expm1(t lambda) / N.
 // PADDED: the three factors are zero-padded linear convolutions (no twist) and
 // the padding of each increment is zeroed before it is added.
-template <typename R, int N, int E, bool PADDED, class Ex>
-__device__ __forceinline__ void two_level_pass_incr(C2<R> (&x0)[E], int t, const PassArgs& a, const Ex& ex) {
+//
+// X0 gives x0 element by element (x0.get(e) = element t + e T, see RegX0).
+// On return d holds the total increment.
+template <typename R, int N, int E, bool PADDED, class Ex, class X0>
+__device__ __forceinline__ void two_level_increment(const X0& x0, C2<R> (&d)[E], int t, const PassArgs& a,
+                                                    const Ex& ex) {
     constexpr int T = N / E;
     const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
     const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
     const R* __restrict__ eC = static_cast<const R*>(a.eC);
     const R* __restrict__ eS = static_cast<const R*>(a.eS);
-    C2<R> d[E], y[E];
+    C2<R> y[E];
     if (a.jq_in) {
         const R om = R(a.jq_in_1mE);
 #pragma unroll
-        for (int e = 0; e < E; ++e)
-            d[e] = {jq_increment(x0[e].x, om), jq_increment(x0[e].y, om)};
+        for (int e = 0; e < E; ++e) {
+            const C2<R> v = x0.get(e);
+            d[e] = {jq_increment(v.x, om), jq_increment(v.y, om)};
+        }
     } else {
 #pragma unroll
         for (int e = 0; e < E; ++e) d[e] = {R(0), R(0)};
     }
     // e^{tau/2 C}
 #pragma unroll
-    for (int e = 0; e < E; ++e) y[e] = cadd(x0[e], d[e]);
+    for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
     apply_spectral<R, N, E>(y, t, tw, ex, eC);
     if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
@@ -163,21 +172,21 @@ __device__ __forceinline__ void two_level_pass_incr(C2<R> (&x0)[E], int t, const
     // e^{tau S}
     if constexpr (PADDED) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) y[e] = cadd(x0[e], d[e]);
+        for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
         apply_spectral<R, N, E>(y, t, tw, ex, eS);
         zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
         for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
     } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e) y[e] = cmul(cadd(x0[e], d[e]), ldg_c2(twist + t + e * T));
+        for (int e = 0; e < E; ++e) y[e] = cmul(cadd(x0.get(e), d[e]), ldg_c2(twist + t + e * T));
         apply_spectral<R, N, E>(y, t, tw, ex, eS);
 #pragma unroll
         for (int e = 0; e < E; ++e) d[e] = cadd(d[e], cmulc(y[e], ldg_c2(twist + t + e * T)));
     }
     // e^{tau/2 C}
 #pragma unroll
-    for (int e = 0; e < E; ++e) y[e] = cadd(x0[e], d[e]);
+    for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
     apply_spectral<R, N, E>(y, t, tw, ex, eC);
     if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
@@ -186,11 +195,23 @@ __device__ __forceinline__ void two_level_pass_incr(C2<R> (&x0)[E], int t, const
         const R om = R(a.jq_out_1mE);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const C2<R> w = cadd(x0[e], d[e]);
+            const C2<R> w = cadd(x0.get(e), d[e]);
             d[e].x += jq_increment(w.x, om);
             d[e].y += jq_increment(w.y, om);
         }
     }
+}
+
+template <typename R, int E>
+struct RegX0 {
+    const C2<R> (&x)[E];
+    __device__ __forceinline__ C2<R> get(int e) const { return x[e]; }
+};
+
+template <typename R, int N, int E, bool PADDED, class Ex>
+__device__ __forceinline__ void two_level_pass_incr(C2<R> (&x0)[E], int t, const PassArgs& a, const Ex& ex) {
+    C2<R> d[E];
+    two_level_increment<R, N, E, PADDED>(RegX0<R, E>{x0}, d, t, a, ex);
 #pragma unroll
     for (int e = 0; e < E; ++e) x0[e] = cadd(x0[e], d[e]);
 }

@@ -89,6 +89,7 @@ struct sfac_plan {
     } ax[3] = {};
     double3* diag_partial = nullptr;
     double* diag_out = nullptr;
+    unsigned int* status = nullptr;  // SFAC_PASS_TIMEOUT bits set by the passes
     double jq_half_E = 0, jq_half_1mE = 0, jq_full_E = 0, jq_full_1mE = 0;
     void* staging = nullptr;
 };
@@ -132,11 +133,16 @@ sfac_status launch_axis(sfac_plan* P, void* u, int ax, int jq_in, int jq_out, cu
     a.jq_out = jq_out != 0;
     a.jq_out_E = jq_out == 2 ? P->jq_full_E : P->jq_half_E;
     a.jq_out_1mE = jq_out == 2 ? P->jq_full_1mE : P->jq_half_1mE;
+    a.status = P->status;
     cudaError_t err;
-    if (P->ax[ax].padded)
+    if (P->ax[ax].padded) {
         err = (P->p.prec == SFAC_FP64) ? sfac::launch_pass_padded_f64(N, a, st) : sfac::launch_pass_padded_f32(N, a, st);
-    else
-        err = (P->p.prec == SFAC_FP64) ? sfac::launch_pass_f64(N, a, st) : sfac::launch_pass_f32(N, a, st);
+    } else if (P->p.prec == SFAC_FP64) {
+        err = sfac::launch_pass_f64(N, a, st);
+    } else {
+        err = sfac::launch_pass_staged_f32(N, a, st);
+        if (err == cudaErrorNotSupported) err = sfac::launch_pass_f32(N, a, st);
+    }
     if (err != cudaSuccess) return cuda_fail(err, "axis pass launch");
     return SFAC_OK;
 }
@@ -252,6 +258,8 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
     total += align256(sizeof(double3) * (size_t)max_partials);
     const size_t off_out = total;
     total += align256(4 * sizeof(double));
+    const size_t off_status = total;
+    total += align256(sizeof(unsigned int));
     std::vector<unsigned char> blob;
     try {
         blob.assign(total, 0);
@@ -327,6 +335,7 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
     }
     P->diag_partial = reinterpret_cast<double3*>(base + off_partial);
     P->diag_out = reinterpret_cast<double*>(base + off_out);
+    P->status = reinterpret_cast<unsigned int*>(base + off_status);
     *out = P;
     return SFAC_OK;
 }
@@ -372,6 +381,41 @@ sfac_status sfac_plan_info(const sfac_plan* plan, int axis, int* fft_len, int* p
     if (fft_len) *fft_len = plan->ax[axis].fft_len;
     if (padded) *padded = plan->ax[axis].padded ? 1 : 0;
     return SFAC_OK;
+}
+
+sfac_status sfac_plan_kernel(const sfac_plan* plan, int axis, const void* u_dev, int* kind) {
+    if (!plan || axis < 0 || axis >= plan->p.dim || !kind) return fail(SFAC_EINVAL, "bad plan, axis or kind");
+    long long inner = 1;
+    for (int l = 0; l < axis; ++l) inner *= plan->p.n[l];
+    const int N = plan->ax[axis].fft_len;
+    sfac::PassArgs a;
+    a.u = const_cast<void*>(u_dev);
+    a.inner = inner;
+    a.outer = plan->npts / ((long long)plan->p.n[axis] * inner);
+    a.nmem = plan->p.n[axis];
+    if (plan->p.prec == SFAC_FP32 && !plan->ax[axis].padded && sfac::staged_pass_eligible(N, a))
+        *kind = SFAC_KERNEL_STAGED;
+    else if (plan->p.prec == SFAC_FP32 && N >= 32 && N <= 512)
+        *kind = SFAC_KERNEL_WARP;
+    else
+        *kind = SFAC_KERNEL_CTA;
+    return SFAC_OK;
+}
+
+sfac_status sfac_plan_check(sfac_plan* plan, void* stream) {
+    if (!plan) return fail(SFAC_EINVAL, "plan is NULL");
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned int word = 0;
+    cudaError_t err = cudaMemcpyAsync(&word, plan->status, sizeof(word), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return cuda_fail(err, "status read");
+    if (word == 0) return SFAC_OK;
+    err = cudaMemsetAsync(plan->status, 0, sizeof(word), st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return cuda_fail(err, "status reset");
+    return fail(SFAC_ETIMEOUT, "an axis pass gave up waiting for a staged tile copy; the field is not valid");
 }
 
 sfac_status sfac_diagnostics(sfac_plan* plan, const void* u_dev, double* out, void* stream) {
@@ -447,7 +491,7 @@ sfac_status sfac_step_host(sfac_plan* plan, void* u_host, long long nsteps, void
     if (err != cudaSuccess) return cuda_fail(err, "device-to-host copy");
     err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) return cuda_fail(err, "stream synchronise");
-    return SFAC_OK;
+    return sfac_plan_check(plan, stream);
 }
 
 }  // extern "C"

@@ -60,6 +60,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sfac_axis_pass": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]),
         "sfac_diagnostics": (ctypes.c_int, [vp, vp, P(d), vp]),
         "sfac_plan_info": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]),
+        "sfac_plan_kernel": (ctypes.c_int, [vp, ctypes.c_int, vp, P(ctypes.c_int)]),
+        "sfac_plan_check": (ctypes.c_int, [vp, vp]),
         "sfac_plan_tables": (ctypes.c_int, [P(SfacParams), ctypes.c_int, P(d), P(d), P(d), P(d)]),
         "sfac_batch_create": (ctypes.c_int, [P(SfacParams), ctypes.c_int, vp, P(vp)]),
         "sfac_batch_destroy": (ctypes.c_int, [vp]),
@@ -174,6 +176,21 @@ def sfac_plan_info(plan: int, axis: int):
     L, pad = ctypes.c_int(), ctypes.c_int()
     _check(load().sfac_plan_info(plan, int(axis), ctypes.byref(L), ctypes.byref(pad)), "sfac_plan_info")
     return L.value, bool(pad.value)
+
+
+SFAC_KERNEL_CTA, SFAC_KERNEL_WARP, SFAC_KERNEL_STAGED = range(3)
+
+
+def sfac_plan_kernel(plan: int, axis: int, u) -> int:
+    """Which kernel (SFAC_KERNEL_*) a pass along `axis` would run for the field u."""
+    kind = ctypes.c_int()
+    _check(load().sfac_plan_kernel(plan, int(axis), _ptr(u), ctypes.byref(kind)), "sfac_plan_kernel")
+    return kind.value
+
+
+def sfac_plan_check(plan: int, stream=None) -> None:
+    """Synchronise; raise SfacError(SFAC_ETIMEOUT) if a pass gave up a bounded wait."""
+    _check(load().sfac_plan_check(plan, _stream(stream)), "sfac_plan_check")
 
 
 def sfac_diagnostics(plan: int, u, stream=None):
@@ -462,6 +479,14 @@ class Plan:
     def step_host(self, u_host, nsteps: int, stream=None):
         sfac_step_host(self.handle, u_host, nsteps, stream)
         return u_host
+
+    def kernel(self, axis: int, u) -> int:
+        """SFAC_KERNEL_* that a pass along `axis` runs for the field u."""
+        return sfac_plan_kernel(self.handle, axis, u)
+
+    def check(self, stream=None):
+        """Synchronise `stream` and raise if a pass gave up a bounded wait."""
+        sfac_plan_check(self.handle, stream)
 
     def close(self):
         if getattr(self, "handle", None):
