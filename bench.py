@@ -62,8 +62,18 @@ FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.07e9 / 1e12
 
 # DRAM bytes (read + write) per launch from ncu, keyed by (workload, precision,
-# axis). None until a capture of the current kernels exists.
-NCU_TRAFFIC = {}
+# axis): the mean of dram__bytes_read.sum + dram__bytes_write.sum over the
+# warm-up and timed launches of
+#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+#       --clock-control none -k regex:axis_pass -c 20|30 --csv
+#       python bench.py --steps 2 --warmup 3 [--workload 3d256] --parity-steps 0 --no-cpu-baseline
+# (profiles/axis_pass_dram_traffic.md). A key must be removed when its kernel changes.
+NCU_TRAFFIC = {
+    ("2d1024", "f64", 0): 8589209, ("2d1024", "f64", 1): 8603596,
+    ("2d1024", "f32", 0): 4298598, ("2d1024", "f32", 1): 4306227,
+    ("3d256", "f64", 0): 203908659, ("3d256", "f64", 1): 209578342, ("3d256", "f64", 2): 209968793,
+    ("3d256", "f32", 0): 71799500, ("3d256", "f32", 1): 76513587, ("3d256", "f32", 2): 76977715,
+}
 
 
 def measured_peaks():

@@ -122,10 +122,24 @@ sfac_status upload_schedule(const std::vector<BatchInst>& inst, int mult, void**
     for (const BatchInst& I : inst) max_steps = std::max<long long>(max_steps, I.steps);
     std::vector<long long> phase_base(1, 0), phase_first(1, 0), slot_cum;
     std::vector<int> phase_step, phase_axis, slot_inst;
+    // Within a phase the slots go by line length, longest first (then by
+    // instance): the warps running at one time then mostly execute the pass
+    // body of one length, instead of all of them at once, which thrashed the
+    // instruction cache when sizes were interleaved.
+    std::vector<int> order[3];
+    for (int a = 0; a < 3; ++a) {
+        order[a].resize(n_inst);
+        for (int i = 0; i < n_inst; ++i) order[a][i] = i;
+        std::stable_sort(order[a].begin(), order[a].end(), [&](int x, int y) {
+            const int nx = a < inst[x].dim ? inst[x].n[a] : 0, ny = a < inst[y].dim ? inst[y].n[a] : 0;
+            return nx > ny;
+        });
+    }
     for (long long s = 0; s < max_steps; ++s) {
         for (int a = 0; a < 3; ++a) {
             long long cum = 0;
-            for (int i = 0; i < n_inst; ++i) {
+            for (int q = 0; q < n_inst; ++q) {
+                const int i = order[a][q];
                 const BatchInst& I = inst[i];
                 if (s < I.steps && a < I.dim) {
                     cum += I.items[a];
