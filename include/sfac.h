@@ -115,6 +115,14 @@ sfac_status sfac_plan_kernel(const sfac_plan* plan, int axis, const void* u_dev,
  * no counterpart. */
 sfac_status sfac_plan_check(sfac_plan* plan, void* stream);
 
+/* Limit of each bounded wait of the plan's passes, in SM clock cycles
+ * (default 2^32, about two seconds at 2.07 GHz; must be >= 1). hold != 0 is a
+ * test hook: the first wait of every CTA of a staged pass then waits for a
+ * barrier that nothing completes, so it runs out after wait_cycles, the pass
+ * records the timeout (see sfac_plan_check) and leaves the field partly
+ * updated. Host-only. The paper has no counterpart. */
+sfac_status sfac_plan_set_wait_limit(sfac_plan* plan, long long wait_cycles, int hold);
+
 /* Release a plan and its device memory. Synchronises the device first so that no
  * enqueued work still reads the tables. NULL is accepted (no-op). */
 sfac_status sfac_plan_destroy(sfac_plan* plan);

@@ -2,7 +2,7 @@
 Allen-Cahn equation (arXiv 2209.08437): a CUDA C-ABI library (libsfac) and
 its thin Python binding."""
 from .sfac import (SFAC_FP32, SFAC_FP64, Batch, Plan, Server, SfacError, SfacParams, load, make_params,  # noqa: F401
-                   sfac_axis_pass, sfac_diagnostics, sfac_plan_info, sfac_plan_kernel, sfac_plan_check,
+                   sfac_axis_pass, sfac_diagnostics, sfac_plan_info, sfac_plan_kernel, sfac_plan_check, sfac_plan_set_wait_limit,
                    SFAC_KERNEL_CTA, SFAC_KERNEL_WARP, SFAC_KERNEL_STAGED, sfac_last_error, sfac_plan_create, sfac_plan_destroy, sfac_plan_tables,
                    sfac_solve, sfac_step, sfac_step_host, sfac_version, sfac_batch_create,
                    sfac_batch_destroy, sfac_batch_prepare, sfac_batch_launch, sfac_batch_wait,

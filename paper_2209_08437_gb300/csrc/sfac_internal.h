@@ -44,6 +44,11 @@ struct PassArgs {
     // Device word where a kernel that gave up waiting for one of its own
     // asynchronous copies records SFAC_PASS_TIMEOUT (NULL: not recorded).
     unsigned int* status = nullptr;
+    // Limit of each such wait in SM clock cycles (about two seconds by
+    // default), and a test hook: hold != 0 makes the first wait of every CTA
+    // wait for a barrier that nothing completes, so that the limit runs out.
+    long long wait_cycles = 4LL << 30;
+    int hold = 0;
 };
 
 constexpr unsigned int SFAC_PASS_TIMEOUT = 1u;

@@ -19,9 +19,10 @@
 // past the last column (inner % BW != 0): the load fills zeros there and the
 // store skips them.
 //
-// Every wait on a load is bounded. A CTA whose wait runs out records
-// SFAC_PASS_TIMEOUT in a.status, stops taking tiles, waits (bounded) for its
-// loads still in flight and for its stores, and returns.
+// Every wait on a load is bounded (a.wait_cycles). A CTA whose wait runs out
+// records SFAC_PASS_TIMEOUT in a.status, stops taking tiles, waits (bounded)
+// for its loads still in flight and for its stores, and returns. The test hook
+// a.hold sends the first wait of every CTA to a barrier nothing completes.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -33,9 +34,6 @@
 namespace sfac {
 
 namespace {
-
-// About two seconds at the GB300's maximum SM clock.
-constexpr long long kWaitCycles = 4LL << 30;
 
 template <int N>
 struct StagedShape {
@@ -54,7 +52,7 @@ struct StagedShape {
     static constexpr int MINB = WPB <= 4 ? 3 : 1;
     static constexpr int XCH_ELEMS = WPB * LPW * WarpExchange<float, N, E>::LINE_ELEMS;
     static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + SmemTables<float, N, false>::BYTES +
-                                   sizeof(C2<float>) * XCH_ELEMS + 8 * STAGES;
+                                   sizeof(C2<float>) * XCH_ELEMS + 8 * (STAGES + 1);
     static_assert(BW == 32 || BW == 16, "tile rows are 64 or 128 bytes");
     static_assert(STAGE_BYTES % 1024 == 0, "stage buffers keep the swizzle atom alignment");
 };
@@ -100,12 +98,13 @@ axis_pass_staged_kernel(const __grid_constant__ CUtensorMap tmap, const PassArgs
     unsigned char* tabs = stage0 + S * Sh::STAGE_BYTES;
     C2<float>* xch = reinterpret_cast<C2<float>*>(tabs + SmemTables<float, N, false>::BYTES);
     uint64_t* full = reinterpret_cast<uint64_t*>(xch + Sh::XCH_ELEMS);
+    uint64_t* never = full + S;  // no arrival ever completes it (the hold test hook)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool leader = threadIdx.x == 0;
     if (leader) {
         prefetch_tensormap(&tmap);
-        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < S + 1; ++s) mbar_init(&full[s], 1);
         fence_mbar_init();
     }
     PassArgs a = a0;
@@ -140,7 +139,8 @@ axis_pass_staged_kernel(const __grid_constant__ CUtensorMap tmap, const PassArgs
     for (; k < mine; ++k) {
         const int s = (int)(k % S);
         unsigned char* buf = stage0 + s * Sh::STAGE_BYTES;
-        const bool ok = mbar_wait_bounded(&full[s], (unsigned)((k / S) & 1), kWaitCycles);
+        const bool held = a0.hold != 0 && k == 0;
+        const bool ok = mbar_wait_bounded(held ? never : &full[s], held ? 0u : (unsigned)((k / S) & 1), a0.wait_cycles);
         const StagedLine<N, E, BW> line{buf, 2 * (warp * LPW + j)};
         C2<float> x[E];
         if (ok) {
@@ -172,7 +172,7 @@ axis_pass_staged_kernel(const __grid_constant__ CUtensorMap tmap, const PassArgs
         if (failed) {
             if (a0.status) atomicOr(a0.status, SFAC_PASS_TIMEOUT);
             for (long long q = k; q < issued; ++q)
-                mbar_wait_bounded(&full[q % S], (unsigned)((q / S) & 1), kWaitCycles);
+                mbar_wait_bounded(&full[q % S], (unsigned)((q / S) & 1), a0.wait_cycles);
         }
         bulk_wait<0>();
     }

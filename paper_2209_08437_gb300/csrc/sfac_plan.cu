@@ -90,6 +90,8 @@ struct sfac_plan {
     double3* diag_partial = nullptr;
     double* diag_out = nullptr;
     unsigned int* status = nullptr;  // SFAC_PASS_TIMEOUT bits set by the passes
+    long long wait_cycles = 4LL << 30;
+    int hold = 0;
     double jq_half_E = 0, jq_half_1mE = 0, jq_full_E = 0, jq_full_1mE = 0;
     void* staging = nullptr;
 };
@@ -134,6 +136,8 @@ sfac_status launch_axis(sfac_plan* P, void* u, int ax, int jq_in, int jq_out, cu
     a.jq_out_E = jq_out == 2 ? P->jq_full_E : P->jq_half_E;
     a.jq_out_1mE = jq_out == 2 ? P->jq_full_1mE : P->jq_half_1mE;
     a.status = P->status;
+    a.wait_cycles = P->wait_cycles;
+    a.hold = P->hold;
     cudaError_t err;
     if (P->ax[ax].padded) {
         err = (P->p.prec == SFAC_FP64) ? sfac::launch_pass_padded_f64(N, a, st) : sfac::launch_pass_padded_f32(N, a, st);
@@ -399,6 +403,13 @@ sfac_status sfac_plan_kernel(const sfac_plan* plan, int axis, const void* u_dev,
         *kind = SFAC_KERNEL_WARP;
     else
         *kind = SFAC_KERNEL_CTA;
+    return SFAC_OK;
+}
+
+sfac_status sfac_plan_set_wait_limit(sfac_plan* plan, long long wait_cycles, int hold) {
+    if (!plan || wait_cycles < 1) return fail(SFAC_EINVAL, "need a plan and wait_cycles >= 1");
+    plan->wait_cycles = wait_cycles;
+    plan->hold = hold != 0;
     return SFAC_OK;
 }
 

@@ -62,6 +62,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sfac_plan_info": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]),
         "sfac_plan_kernel": (ctypes.c_int, [vp, ctypes.c_int, vp, P(ctypes.c_int)]),
         "sfac_plan_check": (ctypes.c_int, [vp, vp]),
+        "sfac_plan_set_wait_limit": (ctypes.c_int, [vp, ll, ctypes.c_int]),
         "sfac_plan_tables": (ctypes.c_int, [P(SfacParams), ctypes.c_int, P(d), P(d), P(d), P(d)]),
         "sfac_batch_create": (ctypes.c_int, [P(SfacParams), ctypes.c_int, vp, P(vp)]),
         "sfac_batch_destroy": (ctypes.c_int, [vp]),
@@ -191,6 +192,11 @@ def sfac_plan_kernel(plan: int, axis: int, u) -> int:
 def sfac_plan_check(plan: int, stream=None) -> None:
     """Synchronise; raise SfacError(SFAC_ETIMEOUT) if a pass gave up a bounded wait."""
     _check(load().sfac_plan_check(plan, _stream(stream)), "sfac_plan_check")
+
+
+def sfac_plan_set_wait_limit(plan: int, wait_cycles: int, hold: int = 0) -> None:
+    """Per-wait limit (SM cycles) of the plan's bounded waits; hold=1 is the test hook."""
+    _check(load().sfac_plan_set_wait_limit(plan, int(wait_cycles), int(hold)), "sfac_plan_set_wait_limit")
 
 
 def sfac_diagnostics(plan: int, u, stream=None):

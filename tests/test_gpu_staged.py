@@ -104,3 +104,28 @@ def test_step_host_checks_status():
         plan.step(u, 3)
         plan.check()
         assert np.array_equal(h, u.cpu().numpy())
+
+
+def test_bounded_tile_wait_runs_out_and_the_plan_stays_usable():
+    """Test hook: the first tile wait of every CTA goes to a barrier that nothing
+    completes. Each CTA gives up after the wait limit (1e5 cycles here), records
+    the timeout, waits for its copies in flight and returns; sfac_plan_check
+    reports SFAC_ETIMEOUT once and clears it, and the plan then runs normally
+    (same result as a fresh plan)."""
+    prob = I.Problem(n=(32, 256, 80), alpha=(1.4, 1.6, 1.5), eps=0.08, tau=1e-3)
+    u0 = I.random_field(prob, 9, -0.9, 0.9).astype(np.float32)
+    with S.Plan.for_problem(prob, S.SFAC_FP32) as plan, S.Plan.for_problem(prob, S.SFAC_FP32) as fresh:
+        u = dev(u0)
+        assert plan.kernel(1, u) == STAGED
+        S.sfac_plan_set_wait_limit(plan.handle, 100_000, 1)
+        plan.axis_pass(u, 1)
+        with pytest.raises(S.SfacError) as ei:
+            plan.check()
+        assert ei.value.status == S.sfac.SFAC_ETIMEOUT
+        plan.check()                                  # the flag was cleared
+        S.sfac_plan_set_wait_limit(plan.handle, 1 << 32, 0)
+        a, b = dev(u0), dev(u0)
+        plan.step(a, 2)
+        fresh.step(b, 2)
+        plan.check()
+        assert torch.equal(a, b)
