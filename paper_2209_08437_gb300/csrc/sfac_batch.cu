@@ -30,12 +30,15 @@ sfac_status bcuda(cudaError_t err, const char* what) {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Kernel shapes the autotuner chooses from: warps per CTA x values per thread
-// for N <= 256 (radix-8 or radix-16 passes) x warp-groups per item.
+// for N <= 256 (radix-8 or radix-16 passes) x warp-groups per item. Shapes of
+// up to 4 warps run a kernel built for three resident CTAs (at most 168
+// registers: more warps, some spilling at N >= 256), 8-warp shapes one built
+// for one CTA (no register cap).
 struct BatchConfig {
     int wpb, es, mult;
 };
 const BatchConfig kConfigs[] = {
-    {4, 16, 1}, {2, 16, 1}, {8, 16, 1}, {4, 8, 1}, {8, 8, 1}, {4, 16, 2},
+    {4, 16, 1}, {2, 16, 1}, {8, 16, 1}, {8, 16, 4}, {8, 8, 1}, {4, 16, 2},
     {8, 16, 2}, {4, 8, 2},  {8, 8, 2},  {4, 16, 4}, {8, 8, 4},  {2, 16, 2},
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);

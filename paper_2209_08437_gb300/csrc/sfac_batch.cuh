@@ -66,24 +66,28 @@ __host__ __device__ constexpr int batch_elems(int N) {
     return N >= 512 ? 16 : ES;
 }
 
-// One warp-group of lines; kept out of line so that each (R, N, E, axis kind)
-// body is compiled once and shared by the batch kernels.
-template <typename R, int N, int E, bool STRIDED>
-__device__ __noinline__ void batch_group(const PassArgs& pa, long long first, C2<R>* region, int lane) {
-    warp_pass_lines<R, N, E, STRIDED, true>(pa, first, region, lane);
-}
-
+// One warp-group of lines (32/T lines, see warp_pass_lines) of either axis
+// kind; kept out of line so that each (R, N, E) body is compiled once per
+// kernel and shared by both axis kinds.
 template <typename R, int N, int E>
-__device__ __forceinline__ void batch_lines(const PassArgs& pa, bool strided, long long first, C2<R>* region,
-                                            int lane) {
-    if (strided) batch_group<R, N, E, true>(pa, first, region, lane);
-    else batch_group<R, N, E, false>(pa, first, region, lane);
+__device__ __noinline__ void batch_lines(const PassArgs& pa, bool strided, long long first, C2<R>* region,
+                                         int lane) {
+    constexpr int T = N / E;
+    using Ex = WarpExchange<R, N, E>;
+    const int j = lane / T, t = lane % T;
+    const LineRefAny<R, N> line(pa, first + j, strided);
+    const Ex ex{region + j * Ex::LINE_ELEMS};
+    C2<R> x[E];
+    line.template load<E>(x, t);
+    fused_pass<R, N, E, false>(x, t, pa, ex);
+    line.template store<E>(x, t);
 }
 
-// Launched with blockDim.x = 32 * (warps per CTA) <= 256 and
-// BATCH_REGION complex values of dynamic shared memory per warp.
-template <typename R, int ES>
-__global__ void __launch_bounds__(256)
+// Launched with blockDim.x = 32 * (warps per CTA) <= MAXT and BATCH_REGION
+// complex values of dynamic shared memory per warp; MINB CTAs per SM must fit
+// the register allocation.
+template <typename R, int ES, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
 batch_kernel(const BatchSchedule b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -179,10 +183,17 @@ namespace sfac {
 // Set the kernel's shared-memory limit and return its persistent grid (one CTA
 // per resident slot on every SM). Called when a run is prepared, outside any
 // stream capture.
+// Kernels of up to 4 warps are compiled for three resident CTAs per SM
+// (FP32; at most 168 registers a thread), 8-warp ones for one.
+template <typename R>
+constexpr int batch_small_minb() {
+    return sizeof(R) == 4 ? 3 : 2;
+}
+
 template <typename R, int ES>
 cudaError_t setup_batch(int wpb, int sms, int* grid) {
     if (wpb < 1 || wpb > 8) return cudaErrorInvalidValue;
-    auto kern = batch_kernel<R, ES>;
+    auto kern = wpb <= 4 ? batch_kernel<R, ES, 128, batch_small_minb<R>()> : batch_kernel<R, ES, 256, 1>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(8 * sizeof(C2<R>) * BATCH_REGION));
     if (err != cudaSuccess) return err;
@@ -199,7 +210,10 @@ template <typename R, int ES>
 cudaError_t launch_batch(int wpb, int grid, const BatchSchedule& sc, cudaStream_t s) {
     if (wpb < 1 || wpb > 8 || grid < 1) return cudaErrorInvalidValue;
     const size_t smem = sizeof(C2<R>) * (size_t)wpb * BATCH_REGION;
-    batch_kernel<R, ES><<<grid, wpb * 32, smem, s>>>(sc);
+    if (wpb <= 4)
+        batch_kernel<R, ES, 128, batch_small_minb<R>()><<<grid, wpb * 32, smem, s>>>(sc);
+    else
+        batch_kernel<R, ES, 256, 1><<<grid, wpb * 32, smem, s>>>(sc);
     return cudaGetLastError();
 }
 

@@ -334,6 +334,90 @@ struct LineRef {
     }
 };
 
+// Lines of either kind, chosen at run time (the batch kernel): one copy of the
+// pass body then serves contiguous and strided passes and only the loads and
+// stores branch, which halves the code the batch kernel keeps in flight.
+// Power-of-two lines (not zero-padded); a strided pass needs an even inner
+// extent (2-vector column pairs). Loads are L2-only (.cg): other SMs wrote the
+// field during the same launch.
+template <typename R, int N>
+struct LineRefAny {
+    R* p0;
+    R* p1;
+    long long stride;
+    bool active;
+    bool strided;
+
+    __device__ __forceinline__ LineRefAny(const PassArgs& a, long long cl, bool strided_) : strided(strided_) {
+        R* u = static_cast<R*>(a.u);
+        active = cl < a.clines;
+        if (strided) {
+            const long long pairs = a.inner >> 1;
+            const long long o = active ? cl / pairs : 0;
+            const long long c = active ? cl - o * pairs : 0;
+            p0 = u + o * (long long)N * a.inner + 2 * c;
+            p1 = p0 + 1;
+            stride = a.inner;
+        } else {
+            const long long r0 = active ? 2 * cl : 0;
+            p0 = u + r0 * N;
+            p1 = (active && r0 + 1 < a.outer) ? p0 + N : nullptr;
+            stride = 1;
+        }
+    }
+
+    template <int E>
+    __device__ __forceinline__ void load(C2<R> (&x)[E], int t) const {
+        using V = typename Vec2T<R>::type;
+        constexpr int T = N / E;
+        if (strided) {
+            const R* q = p0 + t * stride;
+            const long long step = T * stride;
+#pragma unroll
+            for (int e = 0; e < E; ++e, q += step) {
+                if (active) {
+                    const V v = __ldcg(reinterpret_cast<const V*>(q));
+                    x[e] = {v.x, v.y};
+                } else {
+                    x[e] = {R(0), R(0)};
+                }
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = t + e * T;
+                x[e].x = active ? __ldcg(p0 + idx) : R(0);
+                x[e].y = p1 ? __ldcg(p1 + idx) : R(0);
+            }
+        }
+    }
+
+    template <int E>
+    __device__ __forceinline__ void store(const C2<R> (&x)[E], int t) const {
+        using V = typename Vec2T<R>::type;
+        constexpr int T = N / E;
+        if (!active) return;
+        if (strided) {
+            R* q = p0 + t * stride;
+            const long long step = T * stride;
+#pragma unroll
+            for (int e = 0; e < E; ++e, q += step) {
+                V v;
+                v.x = x[e].x;
+                v.y = x[e].y;
+                *reinterpret_cast<V*>(q) = v;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = t + e * T;
+                p0[idx] = x[e].x;
+                if (p1) p1[idx] = x[e].y;
+            }
+        }
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Kernel 1: CTA-synchronised exchanges.
 // ---------------------------------------------------------------------------
