@@ -83,11 +83,7 @@ __device__ __forceinline__ void apply_spectral(C2<R> (&x)[E], int t, const C2<R>
     constexpr int T = N / E;
     line_fft<R, N, E, false>(x, t, tw, ex);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const R s = m[t + e * T];
-        x[e].x *= s;
-        x[e].y *= s;
-    }
+    for (int e = 0; e < E; ++e) x[e] = cscale(x[e], m[t + e * T]);
     line_fft<R, N, E, true>(x, t, tw, ex);
 }
 
