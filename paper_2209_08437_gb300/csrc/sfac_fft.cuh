@@ -27,8 +27,8 @@
 
 namespace sfac {
 
-// A complex value; aligned to its size so that a float pair can sit in one
-// 64-bit register pair (the operand of the packed FP32 instructions).
+// A complex value, aligned to its size: shared-memory exchanges and table reads
+// then move it as one 64-bit (FP32) or 128-bit (FP64) access.
 template <typename R>
 struct alignas(2 * sizeof(R)) C2 {
     R x, y;
@@ -51,47 +51,6 @@ __device__ __forceinline__ C2<R> cmulc(C2<R> a, C2<R> b) {
 // a * s for real s
 template <typename R>
 __device__ __forceinline__ C2<R> cscale(C2<R> a, R s) { return {a.x * s, a.y * s}; }
-
-// FP32 complex arithmetic on the packed two-lane FP32 instructions of sm_100+
-// (__fadd2_rn, __fmul2_rn, __ffma2_rn: each lane rounds exactly as the scalar
-// _rn operation). a - b is fma(b, -1, a), which rounds as the subtraction.
-// SFAC_PACKED_ADD packs sums and differences; SFAC_PACKED_MUL also products.
-#ifndef SFAC_PACKED_ADD
-#define SFAC_PACKED_ADD 1
-#endif
-#ifndef SFAC_PACKED_MUL
-#define SFAC_PACKED_MUL 1
-#endif
-__device__ __forceinline__ float2 as_f2(C2<float> a) { return make_float2(a.x, a.y); }
-__device__ __forceinline__ C2<float> as_c2(float2 v) { return {v.x, v.y}; }
-#if SFAC_PACKED_ADD
-template <>
-__device__ __forceinline__ C2<float> cadd<float>(C2<float> a, C2<float> b) {
-    return as_c2(__fadd2_rn(as_f2(a), as_f2(b)));
-}
-template <>
-__device__ __forceinline__ C2<float> csub<float>(C2<float> a, C2<float> b) {
-    return as_c2(__ffma2_rn(as_f2(b), make_float2(-1.f, -1.f), as_f2(a)));
-}
-#endif
-#if SFAC_PACKED_MUL
-// (a.x b.x - a.y b.y, a.y b.x + a.x b.y) = a * b.x + (-a.y, a.x) * b.y
-template <>
-__device__ __forceinline__ C2<float> cmul<float>(C2<float> a, C2<float> b) {
-    const float2 t = __fmul2_rn(as_f2(a), make_float2(b.x, b.x));
-    return as_c2(__ffma2_rn(make_float2(-a.y, a.x), make_float2(b.y, b.y), t));
-}
-// (a.x b.x + a.y b.y, a.y b.x - a.x b.y) = a * b.x + (a.y, -a.x) * b.y
-template <>
-__device__ __forceinline__ C2<float> cmulc<float>(C2<float> a, C2<float> b) {
-    const float2 t = __fmul2_rn(as_f2(a), make_float2(b.x, b.x));
-    return as_c2(__ffma2_rn(make_float2(a.y, -a.x), make_float2(b.y, b.y), t));
-}
-template <>
-__device__ __forceinline__ C2<float> cscale<float>(C2<float> a, float s) {
-    return as_c2(__fmul2_rn(as_f2(a), make_float2(s, s)));
-}
-#endif
 
 // cos(2 pi q / 32) for q = 1 .. 7 to 21 digits (sin(2 pi q/32) = cos(2 pi (8-q)/32)).
 #define SFAC_C32_1 0.980785280403230449126
