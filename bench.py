@@ -69,10 +69,10 @@ FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.07e9 / 1e12
 #       python bench.py --steps 2 --warmup 3 [--workload 3d256] --parity-steps 0 --no-cpu-baseline
 # (profiles/axis_pass_dram_traffic.md). A key must be removed when its kernel changes.
 NCU_TRAFFIC = {
-    ("2d1024", "f64", 0): 8589209, ("2d1024", "f64", 1): 8603596,
-    ("2d1024", "f32", 0): 4298598, ("2d1024", "f32", 1): 4306227,
-    ("3d256", "f64", 0): 203908659, ("3d256", "f64", 1): 209578342, ("3d256", "f64", 2): 209968793,
-    ("3d256", "f32", 0): 71799500, ("3d256", "f32", 1): 76513587, ("3d256", "f32", 2): 76977715,
+    ("2d1024", "f64", 0): 8583936, ("2d1024", "f64", 1): 8603136,
+    ("2d1024", "f32", 0): 4296192, ("2d1024", "f32", 1): 4307200,
+    ("3d256", "f64", 0): 204113971, ("3d256", "f64", 1): 209806540, ("3d256", "f64", 2): 209815552,
+    ("3d256", "f32", 0): 71865804, ("3d256", "f32", 1): 76532275, ("3d256", "f32", 2): 76980531,
 }
 
 
