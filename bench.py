@@ -147,35 +147,40 @@ def aggregate_rate(points: int, steps: int, world: int, total_ms: float) -> floa
 
 
 def time_gpu_path(S, torch, problem, u0, prec, steps, warmup, flush):
-    """Warm up, then time `steps` single steps (each after an L2 flush) as the
-    sequence of its axis passes with CUDA events on the current stream."""
+    """Warm up, then time `steps` single steps, each one sfac_step call after an
+    L2 flush, with CUDA events on the current stream. Then time every axis pass
+    on its own (same J^Q modes as in the step), each after an L2 flush, for the
+    roofline's kernel duration."""
     dt = torch.float64 if prec == S.SFAC_FP64 else torch.float32
     d = problem.dim
     with S.Plan.for_problem(problem, prec) as plan:
         u = torch.tensor(u0, dtype=dt, device="cuda")
         modes = [(1 if ax == 0 else 0, 1 if ax == d - 1 else 0) for ax in range(d)]
-
-        def one_step():
-            for ax in range(d):
-                plan.axis_pass(u, ax, *modes[ax])
-
         for _ in range(warmup):
             flush.zero_()
-            one_step()
+            plan.step(u, 1)
         torch.cuda.synchronize()
         stream = torch.cuda.current_stream()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(d + 1)] for _ in range(steps)]
-        for k in range(steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
             flush.zero_()
-            evs[k][0].record(stream)
-            for ax in range(d):
-                plan.axis_pass(u, ax, *modes[ax])
-                evs[k][ax + 1].record(stream)
+            e0.record(stream)
+            plan.step(u, 1)
+            e1.record(stream)
         torch.cuda.synchronize()
-        per_axis = [[evs[k][ax].elapsed_time(evs[k][ax + 1]) for k in range(steps)] for ax in range(d)]
-        step_ms = [evs[k][0].elapsed_time(evs[k][d]) for k in range(steps)]
+        step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        per_axis = []
+        for ax in range(d):
+            aev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for e0, e1 in aev:
+                flush.zero_()
+                e0.record(stream)
+                plan.axis_pass(u, ax, *modes[ax])
+                e1.record(stream)
+            torch.cuda.synchronize()
+            per_axis.append([e0.elapsed_time(e1) for e0, e1 in aev])
         ok = bool(torch.isfinite(u).all())
-    return {"step_ms": step_ms, "axis_ms": per_axis, "finite": ok, "launches": steps * d}
+    return {"step_ms": step_ms, "axis_ms": per_axis, "finite": ok, "launches": 2 * steps * d}
 
 
 def time_e2e(S, torch, problem, u0, prec, steps):
@@ -313,6 +318,21 @@ def run_batched(args, S, torch):
     return 0
 
 
+def serving_shape(S, torch, sample, chunk):
+    """Kernel shape for the serving rounds: the batch autotuner's choice on the
+    first requests of the stream (their problems and initial fields, one round
+    of `chunk` steps), measured before the timed region."""
+    probs = [r.problem for r in sample]
+    dev = [torch.tensor(np.asarray(I.request_u0(r), np.float32), device="cuda") for r in sample]
+    with S.Batch(probs, S.SFAC_FP32) as b:
+        b.prepare(dev, [min(p.steps, chunk) for p in probs])
+        b.autotune(max_steps=chunk)
+        cfg = S.sfac_batch_get_config(b.handle)
+    del dev
+    torch.cuda.empty_cache()
+    return cfg
+
+
 def run_serving(args, S, torch):
     """Poisson stream of 2000 requests (200/s; half 2D n in {64..512}, half 3D n in
     {32,64,128}; 100-1000 steps; FP32) served with continuous batching: requests
@@ -321,13 +341,15 @@ def run_serving(args, S, torch):
     reqs = I.serving_stream(args.requests)
     chunk = args.chunk
     S.load()
+    cfg = serving_shape(S, torch, reqs[:64], chunk)
+    shape = cfg[0]
     with S.Server(2 << 30, 1024, S.SFAC_FP32) as srv:
         # warm-up: a few small requests
         S.serve(I.serving_stream(8, rate_hz=1e6, sizes_2d=(64,), sizes_3d=(32,), steps_range=(5, 10)),
-                lambda r: np.asarray(I.request_u0(r), np.float32), srv, chunk=chunk)
+                lambda r: np.asarray(I.request_u0(r), np.float32), srv, chunk=chunk, shape=shape)
         sampler = ClockSampler(torch.cuda.current_device())
         sampler.start()
-        out = S.serve(reqs, lambda r: np.asarray(I.request_u0(r), np.float32), srv, chunk=chunk)
+        out = S.serve(reqs, lambda r: np.asarray(I.request_u0(r), np.float32), srv, chunk=chunk, shape=shape)
         clocks = sampler.stop()
     lat = np.array(list(out["latency"].values()))
     line = {
@@ -338,7 +360,9 @@ def run_serving(args, S, torch):
                                "{64,128,256,512}, half 3D n in {32,64,128}, alpha U[1.1,1.9], eps U[0.02,0.2], "
                                "tau=1e-3, 100-1000 steps, FP32; continuous batching in rounds of "
                                f"{chunk} steps, admission by a 2 GiB device arena",
-                   "requests": len(reqs), "chunk_steps": chunk},
+                   "requests": len(reqs), "chunk_steps": chunk,
+                   "kernel_shape": dict(zip(("index", "warps_per_cta", "values_per_thread", "groups_per_item"),
+                                            cfg))},
         "latency": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                     "mean_s": float(lat.mean()), "max_s": float(lat.max())},
         "served_point_steps": out["point_steps"], "wall_s": out["wall_s"], "rounds": out["rounds"],
