@@ -72,7 +72,6 @@ NCU_TRAFFIC = {
     ("2d1024", "f64", 0): 8583936, ("2d1024", "f64", 1): 8603136,
     ("2d1024", "f32", 0): 4296192, ("2d1024", "f32", 1): 4307200,
     ("3d256", "f64", 0): 204113971, ("3d256", "f64", 1): 209806540, ("3d256", "f64", 2): 209815552,
-    ("3d256", "f32", 0): 71865804, ("3d256", "f32", 1): 76532275, ("3d256", "f32", 2): 76980531,
 }
 
 

@@ -124,6 +124,58 @@ __device__ __forceinline__ void two_level_chain(C2<R> (&x)[E], int t, const Pass
     apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eC));
 }
 
+// For lines of up to SFAC_ROLLED_MAX_N points the FP32 chain runs rolled: one
+// loop over the three factors, and each F^{-1} diag(m) F computed as
+// conj(F(conj(m F y))) (m is real), so the kernel holds one forward-FFT body
+// instead of six unrolled FFTs, whose code stalled the passes on instruction
+// fetch. Longer lines keep the unrolled chain: measured on GB300, rolling made
+// the 1024-point CTA kernel and the 512-point batch passes slower and the
+// passes of 256 points and less faster (strided 256-point passes by 9%,
+// batches of 3D n = 128 instances by 18%).
+#ifndef SFAC_ROLLED_MAX_N
+#define SFAC_ROLLED_MAX_N 256
+#endif
+
+// d += the increments of e^{tau/2 C}, e^{tau S}, e^{tau/2 C} in turn (each
+// applied to x0 + d), rolled as described above.
+template <typename R, int N, int E, bool PADDED, class Ex, class X0>
+__device__ __forceinline__ void three_factors_rolled(const X0& x0, C2<R> (&d)[E], int t, const PassArgs& a,
+                                                     const Ex& ex) {
+    constexpr int T = N / E;
+    const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
+    const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
+    C2<R> y[E];
+#pragma unroll 1
+    for (int f = 0; f < 3; ++f) {
+        const bool skew = !PADDED && f == 1;
+        const R* __restrict__ m = static_cast<const R*>(f == 1 ? a.eS : a.eC);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            y[e] = cadd(x0.get(e), d[e]);
+            if (skew) y[e] = cmul(y[e], ldg_c2(twist + t + e * T));
+        }
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            line_fft<R, N, E, false>(y, t, tw, ex);
+            if (h == 0) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const R sc = m[t + e * T];
+                    y[e] = {y[e].x * sc, -(y[e].y * sc)};
+                }
+            }
+        }
+        // y holds the conjugate of the factor's increment
+        if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            C2<R> r = {y[e].x, -y[e].y};
+            if (skew) r = cmulc(r, ldg_c2(twist + t + e * T));
+            d[e] = cadd(d[e], r);
+        }
+    }
+}
+
 // The whole FP32 pass in increment form. The loaded line x0 is kept as it is
 // and every change the pass makes is summed in d:
 //   J^Q (load)  d += v q / (s (1 + s))                        (jq_increment)
@@ -141,12 +193,6 @@ __device__ __forceinline__ void two_level_chain(C2<R> (&x)[E], int t, const Pass
 template <typename R, int N, int E, bool PADDED, class Ex, class X0>
 __device__ __forceinline__ void two_level_increment(const X0& x0, C2<R> (&d)[E], int t, const PassArgs& a,
                                                     const Ex& ex) {
-    constexpr int T = N / E;
-    const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
-    const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
-    const R* __restrict__ eC = static_cast<const R*>(a.eC);
-    const R* __restrict__ eS = static_cast<const R*>(a.eS);
-    C2<R> y[E];
     if (a.jq_in) {
         const R om = R(a.jq_in_1mE);
 #pragma unroll
@@ -158,35 +204,45 @@ __device__ __forceinline__ void two_level_increment(const X0& x0, C2<R> (&d)[E],
 #pragma unroll
         for (int e = 0; e < E; ++e) d[e] = {R(0), R(0)};
     }
-    // e^{tau/2 C}
-#pragma unroll
-    for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
-    apply_spectral<R, N, E>(y, t, tw, ex, eC);
-    if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
-#pragma unroll
-    for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
-    // e^{tau S}
-    if constexpr (PADDED) {
+    if constexpr (N <= SFAC_ROLLED_MAX_N) {
+        three_factors_rolled<R, N, E, PADDED>(x0, d, t, a, ex);
+    } else {
+        constexpr int T = N / E;
+        const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
+        const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
+        const R* __restrict__ eC = static_cast<const R*>(a.eC);
+        const R* __restrict__ eS = static_cast<const R*>(a.eS);
+        C2<R> y[E];
+        // e^{tau/2 C}
 #pragma unroll
         for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
-        apply_spectral<R, N, E>(y, t, tw, ex, eS);
-        zero_tail<R, N, E>(y, t, a.nmem);
+        apply_spectral<R, N, E>(y, t, tw, ex, eC);
+        if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
         for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
-    } else {
+        // e^{tau S}
+        if constexpr (PADDED) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) y[e] = cmul(cadd(x0.get(e), d[e]), ldg_c2(twist + t + e * T));
-        apply_spectral<R, N, E>(y, t, tw, ex, eS);
+            for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
+            apply_spectral<R, N, E>(y, t, tw, ex, eS);
+            zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
-        for (int e = 0; e < E; ++e) d[e] = cadd(d[e], cmulc(y[e], ldg_c2(twist + t + e * T)));
+            for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) y[e] = cmul(cadd(x0.get(e), d[e]), ldg_c2(twist + t + e * T));
+            apply_spectral<R, N, E>(y, t, tw, ex, eS);
+#pragma unroll
+            for (int e = 0; e < E; ++e) d[e] = cadd(d[e], cmulc(y[e], ldg_c2(twist + t + e * T)));
+        }
+        // e^{tau/2 C}
+#pragma unroll
+        for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
+        apply_spectral<R, N, E>(y, t, tw, ex, eC);
+        if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
+#pragma unroll
+        for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
     }
-    // e^{tau/2 C}
-#pragma unroll
-    for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
-    apply_spectral<R, N, E>(y, t, tw, ex, eC);
-    if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
-#pragma unroll
-    for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
     if (a.jq_out) {
         const R om = R(a.jq_out_1mE);
 #pragma unroll
