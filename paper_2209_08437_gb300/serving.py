@@ -4,10 +4,11 @@ by device memory.
 Requests arrive at their `arrival_s` times (scaled by `time_scale`, replayed
 against the wall clock). Arrived requests are admitted in arrival order while
 the server has a free slot and arena block (the library computes their FP64
-tables and uploads field and tables); admission happens while the previous
-round runs on the GPU. Each round advances every admitted request by up to
-`chunk` steps in one persistent launch; finished requests are copied back and
-their slots freed, which lets queued requests in. Latency is completion time
+tables and uploads field and tables). Each round advances every admitted request
+by up to `chunk` steps in one persistent launch; a round is launched as soon as
+the previous one has finished, and admission (host work) runs while it is on
+the GPU, so requests admitted then join the next round. Finished requests are
+copied back and their slots freed, which lets queued requests in. Latency is completion time
 minus arrival time.
 """
 from __future__ import annotations
@@ -54,6 +55,11 @@ def serve(requests, make_u0, server: "_s.Server", chunk: int = 100, shape: int =
     in_flight = False
     while pending or queue or slot_req:
         arrive()
+        if not in_flight and slot_req:
+            # the next round goes out first, so the GPU does not wait for admission
+            server.round(chunk, shape, stream)
+            rounds += 1
+            in_flight = True
         admit()                                    # overlaps the round in flight, if any
         if in_flight:
             finished = server.wait(stream)
@@ -67,11 +73,7 @@ def serve(requests, make_u0, server: "_s.Server", chunk: int = 100, shape: int =
                 if keep_results:
                     results[r.rid] = out
             continue
-        if slot_req:
-            server.round(chunk, shape, stream)
-            rounds += 1
-            in_flight = True
-        elif pending:
+        if not slot_req and pending:
             time.sleep(max(0.0, min(0.01, pending[0].arrival_s * time_scale - now())))
     wall = now()
     lat = np.array([latency[r.rid] for r in requests]) if requests else np.zeros(1)
