@@ -70,3 +70,46 @@ def test_fifo_admission_backpressure_and_latency():
         assert np.all(out["results"][r.rid] == r.problem.steps)
     assert out["point_steps"] == sum(r.problem.points * r.problem.steps for r in reqs)
     assert out["p99_s"] >= out["p50_s"] >= 0
+
+
+class LoggingServer(FakeServer):
+    """FakeServer that records the order of its calls."""
+
+    def __init__(self, *a):
+        super().__init__(*a)
+        self.log = []
+
+    def admit(self, problem, u0, nsteps):
+        slot = super().admit(problem, u0, nsteps)
+        self.log.append("admit" if slot is not None else "admit-full")
+        return slot
+
+    def round(self, chunk, shape=0, stream=None):
+        self.log.append("round")
+        super().round(chunk, shape, stream)
+
+    def wait(self, stream=None):
+        done = super().wait(stream)
+        still = sum(1 for s, v in self.active.items() if v[0] > 0)
+        self.log.append(("wait", still))
+        return done
+
+
+def test_next_round_is_launched_before_admission():
+    """After a round finishes, the loop launches the next round for the slots
+    still active before it admits queued requests (admission is host work that
+    then overlaps the round on the GPU); requests admitted then join the round
+    after."""
+    reqs = I.serving_stream(40, rate_hz=1e6, arrival_seed=5, sizes_2d=(32,), sizes_3d=(32,),
+                            steps_range=(4, 12))
+    srv = LoggingServer(10 ** 9, 6)
+    out = serving.serve(reqs, lambda r: np.zeros(r.problem.shape, np.float32), srv, chunk=2, keep_results=True)
+    assert all(np.all(out["results"][r.rid] == r.problem.steps) for r in reqs)
+    log = srv.log
+    checked = 0
+    for i, call in enumerate(log):
+        if isinstance(call, tuple) and call[1] > 0:
+            # slots still had steps to do: the next call is the round, not an admission
+            assert log[i + 1] == "round", log[i:i + 4]
+            checked += 1
+    assert checked > 0 and "admit" in log
