@@ -111,14 +111,19 @@ void compute_axis_padded(const AxisHost& T, double tau, AxisPadded* P) {
         xc[j] = std::expm1(0.5 * tau * T.lambda[j]);
         xs[j] = std::expm1(tau * T.mu[j]);
     }
-    const long long two_n = 2LL * n;
+    const int two_n = 2 * n;
     for (int d = 0; d < n; ++d) {
         KahanSum sg, sh;
+        // indices (2jd) mod 2n and d(2j - 1) mod 2n, stepped in j (stride 2d)
+        const int step = (2 * d) % two_n;
+        int mg = 0, mh = (two_n - d % two_n) % two_n;
         for (int j = 0; j < n; ++j) {
-            sg.add(xc[j] * cs[(2LL * j * d) % two_n]);
-            long long mm = ((long long)d * (2LL * j - 1)) % two_n;
-            if (mm < 0) mm += two_n;
-            sh.add(xs[j] * cs[mm]);
+            sg.add(xc[j] * cs[mg]);
+            sh.add(xs[j] * cs[mh]);
+            mg += step;
+            if (mg >= two_n) mg -= two_n;
+            mh += step;
+            if (mh >= two_n) mh -= two_n;
         }
         g1[d] = sg.value() / n;
         h1[d] = sh.value() / n;
@@ -189,15 +194,21 @@ void compute_axis(double alpha, double eps, double tau, double a, double b, int 
     // symmetric (c_k = c_{n-k}, s_{-k} = -s_{n-k}); the real parts are summed.
     T->lambda.assign(n, 0.0);
     T->mu.assign(n, 0.0);
-    const long long two_n = 2LL * n;
+    // The angle indices (2jk) mod 2n and k(2j - 1) mod 2n advance by fixed
+    // strides in k; they are stepped instead of recomputed with a division.
+    const int two_n = 2 * n;
     for (int j = 0; j < n; ++j) {
         KahanSum sl, sm;
+        const int dl = (2 * j) % two_n;
+        const int dm = ((2 * j - 1) % two_n + two_n) % two_n;
+        int ml = 0, mm = 0;
         for (int k = 0; k < n; ++k) {
-            const long long ml = (2LL * j * k) % two_n;
-            long long mm = ((long long)k * (2LL * j - 1)) % two_n;
-            if (mm < 0) mm += two_n;
             sl.add(T->cfirst[k] * cs[ml]);
             sm.add(T->sfirst[k] * cs[mm]);
+            ml += dl;
+            if (ml >= two_n) ml -= two_n;
+            mm += dm;
+            if (mm >= two_n) mm -= two_n;
         }
         T->lambda[j] = sl.value();
         T->mu[j] = sm.value();
