@@ -324,3 +324,18 @@ def test_pass_routing(n, expect):
     prob = I.Problem(n=n, alpha=(1.5,) * len(n), eps=0.1, tau=0.01)
     with S.Plan.for_problem(prob) as plan:
         assert [S.sfac_plan_info(plan.handle, ax) for ax in range(len(n))] == expect
+
+
+@pytest.mark.parametrize("n", [(6, 1024), (8, 1024), (16, 2048), (2, 4096)], ids=str)
+def test_fp32_long_strided_lines_match_oracle(n):
+    """FP32 strided passes of 1024+ points run several lines per CTA (4 at
+    1024, 2 at 2048, 1 at 4096); with 3 or 4 line pairs in a CTA the last CTA
+    is partly empty. Max-norm error against the FP64 oracle <= 1e-5."""
+    prob = I.Problem(n=n, alpha=(1.45, 1.6), eps=0.07, tau=1e-3)
+    u0 = I.random_field(prob, 41, -0.9, 0.9)
+    u32 = np.asarray(u0, dtype=np.float32).astype(np.float64)
+    ref = O.solve(prob, u32, 3, route="spectral")
+    got = gpu_run(prob, u32, 3, S.SFAC_FP32)
+    err = float(np.abs(got - ref).max())
+    print(f"{n}: FP32 max-norm error {err:.3e}")
+    assert err <= 1e-5
