@@ -62,6 +62,7 @@ struct sfac_batch {
     int sms = 0;
     std::vector<sfac_params> params;
     void* dev_tables = nullptr;
+    void* dev_common = nullptr;  // twiddles and twists per length (make_common_tables)
     std::vector<sfac::BatchInst> inst;  // tables filled at creation; fields and steps at prepare
     void* dev_sched = nullptr;          // instance array + schedule arrays
     size_t sched_cap = 0;
@@ -209,6 +210,47 @@ sfac_status upload_schedule(const std::vector<BatchInst>& inst, int mult, void**
     return SFAC_OK;
 }
 
+sfac_status make_common_tables(int prec, void** dev) {
+    *dev = nullptr;
+    const bool f64 = prec == SFAC_FP64;
+    const size_t rs = f64 ? sizeof(double) : sizeof(float);
+    std::vector<unsigned char> blob((size_t)BATCH_COMMON_ELEMS * 2 * rs);
+    try {
+        for (int N = 32; N <= 512; N *= 2) {
+            // the same routine as every instance's tables, so the values agree bit for bit
+            AxisHost H;
+            compute_axis(1.5, 0.1, 0.01, -1.0, 1.0, N, &H);
+            const std::vector<double>* src[2] = {&H.twid, &H.twist};
+            for (int q = 0; q < 2; ++q) {
+                const size_t first = 2 * ((size_t)batch_common_offset(N) + (size_t)q * N);  // reals
+                for (size_t k = 0; k < 2 * (size_t)N; ++k) {
+                    const double v = (*src[q])[k];
+                    if (f64) std::memcpy(blob.data() + (first + k) * rs, &v, rs);
+                    else {
+                        const float f = (float)v;
+                        std::memcpy(blob.data() + (first + k) * rs, &f, rs);
+                    }
+                }
+            }
+        }
+    } catch (const std::bad_alloc&) {
+        return bfail(SFAC_ENOMEM, "host allocation failed");
+    }
+    cudaError_t err = cudaMalloc(dev, blob.size());
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        *dev = nullptr;
+        return bfail(SFAC_ENOMEM, std::string("cudaMalloc of the common tables: ") + cudaGetErrorString(err));
+    }
+    err = cudaMemcpy(*dev, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+        cudaFree(*dev);
+        *dev = nullptr;
+        return bcuda(err, "common table upload");
+    }
+    return SFAC_OK;
+}
+
 bool batch_shape(int index, int* wpb, int* es, int* mult) {
     if (index < 0 || index >= kNumConfigs) return false;
     *wpb = kConfigs[index].wpb;
@@ -240,6 +282,7 @@ sfac_status build_schedule(sfac_batch* B, cudaStream_t st) {
     sc.error = reinterpret_cast<int*>(B->dev_scratch + 1 + n_inst);
     sc.spin_limit = B->spin_limit;
     sc.hold_instance = B->hold_instance;
+    sc.common = B->dev_common;
     cudaError_t err = setup_batch(B->prec, c, B->sms, &B->grid);
     if (err != cudaSuccess) return bcuda(err, "batch kernel setup");
     B->prepared = true;
@@ -351,6 +394,13 @@ sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream
                 }
             }
         }
+    {
+        const sfac_status cs = sfac::make_common_tables(B->prec, &B->dev_common);
+        if (cs != SFAC_OK) {
+            sfac_batch_destroy(B);
+            return cs;
+        }
+    }
     cudaError_t err = cudaMalloc(&B->dev_tables, total);
     if (err == cudaSuccess)
         err = cudaMalloc(reinterpret_cast<void**>(&B->dev_scratch), sizeof(unsigned long long) * (size_t)(count + 2));
@@ -399,6 +449,7 @@ sfac_status sfac_batch_destroy(sfac_batch* B) {
     if (prev != B->device) cudaSetDevice(B->device);
     cudaDeviceSynchronize();
     if (B->dev_tables) cudaFree(B->dev_tables);
+    if (B->dev_common) cudaFree(B->dev_common);
     if (B->dev_sched) cudaFree(B->dev_sched);
     if (B->dev_scratch) cudaFree(B->dev_scratch);
     if (B->host_error) cudaFreeHost(B->host_error);

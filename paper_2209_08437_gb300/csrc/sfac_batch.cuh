@@ -83,15 +83,21 @@ __device__ __noinline__ void batch_lines(const PassArgs& pa, bool strided, long 
     line.template store<E>(x, t);
 }
 
-// Launched with blockDim.x = 32 * (warps per CTA) <= MAXT and BATCH_REGION
-// complex values of dynamic shared memory per warp; MINB CTAs per SM must fit
-// the register allocation.
+// Launched with blockDim.x = 32 * (warps per CTA) <= MAXT and dynamic shared
+// memory for BATCH_REGION complex values per warp plus BATCH_COMMON_ELEMS;
+// MINB CTAs per SM must fit the register allocation.
 template <typename R, int ES, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
 batch_kernel(const BatchSchedule b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     C2<R>* region = reinterpret_cast<C2<R>*>(smem_raw) + warp * BATCH_REGION;
+    // Twiddles and twists of every length, shared by all instances, read from
+    // shared memory instead of each instance's global copy.
+    C2<R>* common = reinterpret_cast<C2<R>*>(smem_raw) + (blockDim.x >> 5) * BATCH_REGION;
+    const C2<R>* gcommon = static_cast<const C2<R>*>(b.common);
+    for (int i = threadIdx.x; i < BATCH_COMMON_ELEMS; i += blockDim.x) common[i] = gcommon[i];
+    __syncthreads();
     int p = 0;  // phase of the last item: claimed items increase, so p only moves forward
     for (;;) {
         unsigned long long item = 0;
@@ -142,8 +148,8 @@ batch_kernel(const BatchSchedule b) {
         pa.nmem = N;
         pa.eC = I.tab[a][0];
         pa.eS = I.tab[a][1];
-        pa.twist = I.tab[a][2];
-        pa.twid = I.tab[a][3];
+        pa.twid = common + batch_common_offset(N);
+        pa.twist = common + batch_common_offset(N) + N;
         // J^Q_{tau/2} opens step 0 and closes the last step; inner steps merge
         // the closing and opening halves into J^Q_tau.
         pa.jq_in = (a == 0 && s == 0);
@@ -195,9 +201,9 @@ cudaError_t setup_batch(int wpb, int sms, int* grid) {
     if (wpb < 1 || wpb > 8) return cudaErrorInvalidValue;
     auto kern = wpb <= 4 ? batch_kernel<R, ES, 128, batch_small_minb<R>()> : batch_kernel<R, ES, 256, 1>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(8 * sizeof(C2<R>) * BATCH_REGION));
+                                           (int)(sizeof(C2<R>) * (8 * BATCH_REGION + BATCH_COMMON_ELEMS)));
     if (err != cudaSuccess) return err;
-    const size_t smem = sizeof(C2<R>) * (size_t)wpb * BATCH_REGION;
+    const size_t smem = sizeof(C2<R>) * ((size_t)wpb * BATCH_REGION + BATCH_COMMON_ELEMS);
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
     if (err != cudaSuccess) return err;
@@ -209,7 +215,7 @@ cudaError_t setup_batch(int wpb, int sms, int* grid) {
 template <typename R, int ES>
 cudaError_t launch_batch(int wpb, int grid, const BatchSchedule& sc, cudaStream_t s) {
     if (wpb < 1 || wpb > 8 || grid < 1) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(C2<R>) * (size_t)wpb * BATCH_REGION;
+    const size_t smem = sizeof(C2<R>) * ((size_t)wpb * BATCH_REGION + BATCH_COMMON_ELEMS);
     if (wpb <= 4)
         batch_kernel<R, ES, 128, batch_small_minb<R>()><<<grid, wpb * 32, smem, s>>>(sc);
     else

@@ -38,7 +38,18 @@ struct BatchSchedule {
     int* error;                    // 0, or SFAC_BATCH_TIMEOUT
     long long spin_limit;          // polls before a wait gives up
     int hold_instance;             // test hook: this instance's second pass never becomes ready (-1: off)
+    const void* common;            // twiddles and twists of every length (batch_common_offset), precision R
 };
+
+// Twiddles e^{-2 pi i k/N} and twists e^{i pi k/N} depend on the line length
+// only. One device block holds them for N = 32 .. 512, as complex values of the
+// batch's precision: at batch_common_offset(N) the N twiddles, then the N
+// twists. Each CTA of the batch kernel copies the block into shared memory.
+constexpr int BATCH_COMMON_ELEMS = 2 * (32 + 64 + 128 + 256 + 512);
+__host__ __device__ constexpr int batch_common_offset(int N) { return 2 * (N - 32); }
+
+// Allocate and fill that block for precision `prec` (synchronous upload).
+sfac_status make_common_tables(int prec, void** dev);
 
 constexpr int SFAC_BATCH_TIMEOUT = 1;
 

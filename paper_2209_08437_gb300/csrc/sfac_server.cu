@@ -127,6 +127,7 @@ struct sfac_server {
     std::vector<Slot> slots;
     cudaStream_t copy_stream = nullptr;
     void* dev_sched = nullptr;
+    void* dev_common = nullptr;  // twiddles and twists per length (make_common_tables)
     size_t sched_cap = 0;
     unsigned long long* scratch = nullptr;  // counter, done[max_slots], error
     int* host_error = nullptr;
@@ -161,6 +162,13 @@ sfac_status sfac_server_create(size_t arena_bytes, int max_slots, int prec, void
         sfac_server_destroy(S);
         return sfail(SFAC_ENOMEM, std::string("server allocation: ") + cudaGetErrorString(err));
     }
+    {
+        const sfac_status cs = sfac::make_common_tables(prec, &S->dev_common);
+        if (cs != SFAC_OK) {
+            sfac_server_destroy(S);
+            return cs;
+        }
+    }
     *S->host_error = 0;
     S->arena.init(arena_bytes);
     S->slots.resize(max_slots);
@@ -174,6 +182,7 @@ sfac_status sfac_server_destroy(sfac_server* S) {
     if (S->arena_mem) cudaFree(S->arena_mem);
     if (S->scratch) cudaFree(S->scratch);
     if (S->dev_sched) cudaFree(S->dev_sched);
+    if (S->dev_common) cudaFree(S->dev_common);
     if (S->host_error) cudaFreeHost(S->host_error);
     if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
     delete S;
@@ -296,6 +305,7 @@ sfac_status sfac_server_round(sfac_server* S, long long chunk, int shape, void* 
     S->sc.error = reinterpret_cast<int*>(S->scratch + 1 + (long long)S->slots.size());
     S->sc.spin_limit = S->spin_limit;
     S->sc.hold_instance = -1;
+    S->sc.common = S->dev_common;
     cudaError_t err = S->prec == SFAC_FP64 ? sfac::setup_batch_f64(wpb, es, S->sms, &S->grid)
                                            : sfac::setup_batch_f32(wpb, es, S->sms, &S->grid);
     if (err == cudaSuccess)
