@@ -70,7 +70,9 @@ FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.07e9 / 1e12
 # (profiles/axis_pass_dram_traffic.md). A key must be removed when its kernel changes.
 NCU_TRAFFIC = {
     ("2d1024", "f64", 0): 8583936, ("2d1024", "f64", 1): 8603136,
+    ("2d1024", "f32", 0): 4284598, ("2d1024", "f32", 1): 4285513,
     ("3d256", "f64", 0): 204113971, ("3d256", "f64", 1): 209806540, ("3d256", "f64", 2): 209815552,
+    ("3d256", "f32", 0): 72380342, ("3d256", "f32", 1): 75123309, ("3d256", "f32", 2): 75733504,
 }
 
 
