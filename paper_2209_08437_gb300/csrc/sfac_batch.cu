@@ -368,24 +368,25 @@ sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream
     }
     const bool f64 = B->prec == SFAC_FP64;
     const size_t rs = f64 ? sizeof(double) : sizeof(float);
-    std::vector<size_t> off((size_t)count * 12, 0);
+    // Per instance and axis the two spectral factors; twists and twiddles depend
+    // on the length only and live in the common block (make_common_tables).
+    std::vector<size_t> off((size_t)count * 6, 0);
     size_t total = 0;
     for (int i = 0; i < count; ++i)
         for (int a = 0; a < params[i].dim; ++a) {
             const size_t n = (size_t)params[i].n[a];
-            const size_t sz[4] = {n * rs, n * rs, 2 * n * rs, 2 * n * rs};
-            for (int q = 0; q < 4; ++q) {
-                off[((size_t)i * 3 + a) * 4 + q] = total;
-                total += align256(sz[q]);
+            for (int q = 0; q < 2; ++q) {
+                off[((size_t)i * 3 + a) * 2 + q] = total;
+                total += align256(n * rs);
             }
         }
     std::vector<unsigned char> blob(total, 0);
     for (int i = 0; i < count; ++i)
         for (int a = 0; a < params[i].dim; ++a) {
             const sfac::AxisHost& H = host[(size_t)i * 3 + a];
-            const std::vector<double>* src[4] = {f64 ? &H.eC : &H.dC, f64 ? &H.eS : &H.dS, &H.twist, &H.twid};
-            for (int q = 0; q < 4; ++q) {
-                unsigned char* dst = blob.data() + off[((size_t)i * 3 + a) * 4 + q];
+            const std::vector<double>* src[2] = {f64 ? &H.eC : &H.dC, f64 ? &H.eS : &H.dS};
+            for (int q = 0; q < 2; ++q) {
+                unsigned char* dst = blob.data() + off[((size_t)i * 3 + a) * 2 + q];
                 if (f64) {
                     std::memcpy(dst, src[q]->data(), src[q]->size() * sizeof(double));
                 } else {
@@ -429,7 +430,7 @@ sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream
         for (int a = 0; a < 3; ++a) {
             I.n[a] = a < p.dim ? p.n[a] : 1;
             I.npts *= I.n[a];
-            for (int q = 0; q < 4; ++q) I.tab[a][q] = a < p.dim ? base + off[((size_t)i * 3 + a) * 4 + q] : nullptr;
+            for (int q = 0; q < 2; ++q) I.tab[a][q] = a < p.dim ? base + off[((size_t)i * 3 + a) * 2 + q] : nullptr;
         }
         I.jq[0] = std::exp(-p.tau);
         I.jq[1] = -std::expm1(-p.tau);

@@ -18,7 +18,7 @@ struct BatchInst {
     int steps;              // steps of this run
     int n[3];
     int items[3];           // work items of one pass along each axis
-    const void* tab[3][4];  // per axis: eC, eS, twist, twiddles (see PassArgs)
+    const void* tab[3][2];  // per axis: eC, eS (see PassArgs); twists and twiddles: BatchSchedule::common
     double jq[4];           // e^{-tau}, 1 - e^{-tau}, e^{-2 tau}, 1 - e^{-2 tau}
 };
 

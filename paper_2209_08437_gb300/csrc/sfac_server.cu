@@ -98,7 +98,7 @@ size_t request_bytes(const sfac_params& p) {
     size_t pts = 1;
     for (int a = 0; a < p.dim; ++a) pts *= (size_t)p.n[a];
     size_t b = al256(pts * rs);
-    for (int a = 0; a < p.dim; ++a) b += 2 * al256((size_t)p.n[a] * rs) + 2 * al256(2 * (size_t)p.n[a] * rs);
+    for (int a = 0; a < p.dim; ++a) b += 2 * al256((size_t)p.n[a] * rs);  // eC, eS per axis
     return b;
 }
 
@@ -234,8 +234,8 @@ sfac_status sfac_server_admit(sfac_server* S, const sfac_params* params, const v
             if (a >= p.dim) continue;
             sfac::AxisHost H;
             sfac::compute_axis(p.alpha[a], p.eps, p.tau, p.a, p.b, p.n[a], &H);
-            const std::vector<double>* src[4] = {f64 ? &H.eC : &H.dC, f64 ? &H.eS : &H.dS, &H.twist, &H.twid};
-            for (int q = 0; q < 4; ++q) {
+            const std::vector<double>* src[2] = {f64 ? &H.eC : &H.dC, f64 ? &H.eS : &H.dS};
+            for (int q = 0; q < 2; ++q) {
                 unsigned char* dst = blob.data() + cur;
                 if (f64) {
                     std::memcpy(dst, src[q]->data(), src[q]->size() * sizeof(double));
