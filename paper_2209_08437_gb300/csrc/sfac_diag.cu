@@ -144,12 +144,10 @@ cudaError_t launch_diag_cfg(const PassArgs& a, const double* mA, const double* m
     using Ex = PadExchange<double, N, LPC, STRIDED>;
     const size_t smem = sizeof(C2<double>) * (size_t)Ex::elems();
     auto kern = diag_pass_kernel<Rin, N, STRIDED, PADDED>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        configured = true;
-    }
+    static LaunchSetup setup;
+    int dev = 0;
+    const cudaError_t err = set_smem(kern, smem, setup, &dev);
+    if (err != cudaSuccess) return err;
     const long long grid = (a.clines + LPC - 1) / LPC;
     *nblocks = grid;
     if (grid <= 0) return cudaSuccess;

@@ -21,6 +21,8 @@
 //    exchanges need only warp-level synchronisation (FP32, 32 <= N <= 1024).
 #pragma once
 
+#include <atomic>
+
 #include "sfac_fft.cuh"
 #include "sfac_internal.h"
 
@@ -603,12 +605,42 @@ constexpr int elems_per_thread() {
     return N >= 2048 ? 16 : (N < 8 ? N : 8);
 }
 
+// Per-kernel launch set-up, done once per device: the shared-memory attribute
+// (cudaFuncSetAttribute acts on the current device only) and, for persistent
+// kernels, the resident grid (CTAs per SM x SMs).
+struct LaunchSetup {
+    static constexpr int kMaxDevices = 64;
+    std::atomic<unsigned long long> configured{0};  // bit d: attribute set on device d
+    std::atomic<int> resident[kMaxDevices] = {};
+};
+
 template <class K>
-cudaError_t set_smem(K kern, size_t smem, bool& configured) {
-    if (configured) return cudaSuccess;
-    const cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err == cudaSuccess) configured = true;
+cudaError_t set_smem(K kern, size_t smem, LaunchSetup& ls, int* dev_out) {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= LaunchSetup::kMaxDevices) return cudaErrorInvalidDevice;
+    *dev_out = dev;
+    if ((ls.configured.load() >> dev) & 1ULL) return cudaSuccess;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess) ls.configured.fetch_or(1ULL << dev);
     return err;
+}
+
+// Resident grid of a persistent kernel on device `dev` (computed once).
+template <class K>
+cudaError_t resident_grid(K kern, int threads, size_t smem, LaunchSetup& ls, int dev, int* grid) {
+    int r = ls.resident[dev].load();
+    if (r == 0) {
+        int sms = 0, per_sm = 0;
+        cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        if (err != cudaSuccess) return err;
+        r = (per_sm < 1 ? 1 : per_sm) * (sms < 1 ? 1 : sms);
+        ls.resident[dev].store(r);
+    }
+    *grid = r;
+    return cudaSuccess;
 }
 
 template <typename R, int N, int E, int LPC, bool STRIDED, bool PADDED>
@@ -620,8 +652,9 @@ cudaError_t launch_cfg(const PassArgs& a, cudaStream_t s) {
     using Ex = PadExchange<R, N, LPC, STRIDED>;
     const size_t smem = sizeof(C2<R>) * (size_t)Ex::elems();
     auto kern = axis_pass_kernel<R, N, E, LPC, STRIDED, MINB, PADDED>;
-    static bool configured = false;
-    cudaError_t err = set_smem(kern, smem, configured);
+    static LaunchSetup setup;
+    int dev = 0;
+    cudaError_t err = set_smem(kern, smem, setup, &dev);
     if (err != cudaSuccess) return err;
     const long long grid = (a.clines + LPC - 1) / LPC;
     if (grid <= 0) return cudaSuccess;
@@ -636,18 +669,11 @@ cudaError_t launch_warp(const PassArgs& a, cudaStream_t s) {
     const size_t smem = SmemTables<R, N, PADDED>::BYTES +
                         sizeof(C2<R>) * (size_t)WPB * LPW * WarpExchange<R, N, E>::LINE_ELEMS;
     auto kern = axis_pass_warp_kernel<R, N, E, WPB, STRIDED, PADDED>;
-    static bool configured = false;
-    static int resident = 0;  // CTAs per SM x SMs
-    cudaError_t err = set_smem(kern, smem, configured);
+    static LaunchSetup setup;
+    int dev = 0, resident = 0;
+    cudaError_t err = set_smem(kern, smem, setup, &dev);
+    if (err == cudaSuccess) err = resident_grid(kern, WPB * 32, smem, setup, dev, &resident);
     if (err != cudaSuccess) return err;
-    if (resident == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
-        if (err != cudaSuccess) return err;
-        resident = (per_sm < 1 ? 1 : per_sm) * (sms < 1 ? 1 : sms);
-    }
     const long long ngroups = (a.clines + LPW - 1) / LPW;
     if (ngroups <= 0) return cudaSuccess;
     const long long want = (ngroups + WPB - 1) / WPB;

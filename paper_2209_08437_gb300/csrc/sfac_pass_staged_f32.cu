@@ -226,18 +226,11 @@ cudaError_t launch_staged(const PassArgs& a, cudaStream_t s) {
     if (r != CUDA_SUCCESS) return cudaErrorNotSupported;
 
     auto kern = axis_pass_staged_kernel<N>;
-    static bool configured = false;
-    static int resident = 0;
-    cudaError_t err = set_smem(kern, Sh::SMEM, configured);
+    static LaunchSetup setup;
+    int dev = 0, resident = 0;
+    cudaError_t err = set_smem(kern, Sh::SMEM, setup, &dev);
+    if (err == cudaSuccess) err = resident_grid(kern, Sh::WPB * 32, Sh::SMEM, setup, dev, &resident);
     if (err != cudaSuccess) return err;
-    if (resident == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::WPB * 32, Sh::SMEM);
-        if (err != cudaSuccess) return err;
-        resident = (per_sm < 1 ? 1 : per_sm) * (sms < 1 ? 1 : sms);
-    }
     const long long tiles_per_outer = (a.inner + Sh::BW - 1) / Sh::BW;
     const long long ntiles = a.outer * tiles_per_outer;
     if (ntiles <= 0) return cudaSuccess;
@@ -246,16 +239,21 @@ cudaError_t launch_staged(const PassArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// SMs of the current device (cached per device).
 int sm_count() {
-    static const int n = [] {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            return 0;
-        }
-        return sms;
-    }();
-    return n;
+    static std::atomic<int> cache[LaunchSetup::kMaxDevices] = {};
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= LaunchSetup::kMaxDevices) {
+        cudaGetLastError();
+        return 0;
+    }
+    if ((sms = cache[dev].load()) != 0) return sms;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cache[dev].store(sms);
+    return sms;
 }
 
 }  // namespace
