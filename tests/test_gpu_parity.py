@@ -339,3 +339,25 @@ def test_fp32_long_strided_lines_match_oracle(n):
     err = float(np.abs(got - ref).max())
     print(f"{n}: FP32 max-norm error {err:.3e}")
     assert err <= 1e-5
+
+
+@pytest.mark.parametrize("alpha,eps,tau", [((1.01, 1.99), 0.05, 1e-3), ((1.99, 1.01), 0.2, 0.5),
+                                           ((1.5, 1.5), 1e-3, 2.0)], ids=str)
+@pytest.mark.parametrize("prec", [S.SFAC_FP64, S.SFAC_FP32])
+def test_extreme_parameters_match_oracle(alpha, eps, tau, prec):
+    """Orders near both ends of (1, 2), eps from 1e-3 to 0.2, time steps up to
+    2 (solutions that stay O(0.1..1)): the FP64 path stays within 1e-12
+    (relative max-norm) of the oracle and the FP32 path within 1e-5; max|u| <= 1
+    holds (Theorem 1)."""
+    prob = I.Problem(n=(64, 32), alpha=alpha, eps=eps, tau=tau)
+    u0 = I.random_field(prob, 61, -1.0, 1.0)
+    if prec == S.SFAC_FP32:
+        u0 = u0.astype(np.float32).astype(np.float64)
+    ref = O.solve(prob, u0, 6)
+    got = gpu_run(prob, u0, 6, prec)
+    if prec == S.SFAC_FP64:
+        assert rel_err(got, ref) <= TOL64
+        assert np.abs(got).max() <= 1 + 1e-14
+    else:
+        assert float(np.abs(got - ref).max()) <= 1e-5
+        assert np.abs(got).max() <= 1 + 1e-6
