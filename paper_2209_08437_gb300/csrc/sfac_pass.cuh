@@ -13,12 +13,17 @@
 // with the spectra of Remark 1, all in registers between shared-memory
 // exchanges of the Stockham passes (sfac_fft.cuh).
 //
-// Two kernel shapes share that chain:
+// Kernel shapes that share that chain:
 //  - axis_pass_kernel: a line's T = N/E threads may span several warps, so the
-//    exchanges synchronise the CTA (any N, both precisions);
-//  - axis_pass_warp_kernel: E = 16 or 32 values per thread, so a line of
-//    N <= 1024 points lives inside one warp (with 32/T lines per warp); the
-//    exchanges need only warp-level synchronisation (FP32, 32 <= N <= 1024).
+//    exchanges synchronise the CTA (FP64 at every N; FP32 below 32 and from
+//    1024 points);
+//  - axis_pass_warp_kernel: 16 values per thread, so a line of N <= 512 points
+//    lives inside one warp (with 32/T lines per warp); the exchanges need only
+//    warp-level synchronisation; persistent CTAs keep the tables in shared
+//    memory (FP32, 32 <= N <= 512);
+//  - the TMA-staged kernel of sfac_pass_staged_f32.cu (FP32 strided axes) and
+//    the batch kernel of sfac_batch.cuh run the same warp-local lines.
+// The FP32 chain is the increment form, rolled for N <= SFAC_ROLLED_MAX_N.
 #pragma once
 
 #include <atomic>
@@ -516,7 +521,7 @@ axis_pass_kernel(const PassArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2: warp-local lines (E = 32).
+// Kernel 2: warp-local lines (16 values per thread).
 // ---------------------------------------------------------------------------
 
 // Per-line exchange region of N + N/E complex values: element a is stored at
