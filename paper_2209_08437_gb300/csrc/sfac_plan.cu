@@ -89,7 +89,8 @@ struct sfac_plan {
     } ax[3] = {};
     double3* diag_partial = nullptr;
     double* diag_out = nullptr;
-    unsigned int* status = nullptr;  // SFAC_PASS_TIMEOUT bits set by the passes
+    unsigned int* status = nullptr;       // SFAC_PASS_TIMEOUT bits set by the passes (device)
+    unsigned int* status_host = nullptr;  // pinned host copy of it
     long long wait_cycles = 4LL << 30;
     int hold = 0;
     double jq_half_E = 0, jq_half_1mE = 0, jq_full_E = 0, jq_full_1mE = 0;
@@ -340,6 +341,15 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
     P->diag_partial = reinterpret_cast<double3*>(base + off_partial);
     P->diag_out = reinterpret_cast<double*>(base + off_out);
     P->status = reinterpret_cast<unsigned int*>(base + off_status);
+    err = cudaMallocHost(reinterpret_cast<void**>(&P->status_host), sizeof(unsigned int));
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        P->status_host = nullptr;
+        cudaFree(P->dev_tables);
+        delete P;
+        return fail(SFAC_ENOMEM, std::string("cudaMallocHost of the status word: ") + cudaGetErrorString(err));
+    }
+    *P->status_host = 0;
     *out = P;
     return SFAC_OK;
 }
@@ -353,6 +363,7 @@ sfac_status sfac_plan_destroy(sfac_plan* plan) {
         if (err != cudaSuccess) st = cuda_fail(err, "synchronise before destroy");
         if (plan->dev_tables) cudaFree(plan->dev_tables);
         if (plan->staging) cudaFree(plan->staging);
+        if (plan->status_host) cudaFreeHost(plan->status_host);
     }
     delete plan;
     return st;
@@ -406,6 +417,17 @@ sfac_status sfac_plan_kernel(const sfac_plan* plan, int axis, const void* u_dev,
     return SFAC_OK;
 }
 
+// The status word already copied to plan->status_host and the stream
+// synchronised: clear a recorded timeout and report it.
+static sfac_status status_after_sync(sfac_plan* plan, cudaStream_t st) {
+    if (*plan->status_host == 0) return SFAC_OK;
+    *plan->status_host = 0;
+    cudaError_t err = cudaMemsetAsync(plan->status, 0, sizeof(unsigned int), st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return cuda_fail(err, "status reset");
+    return fail(SFAC_ETIMEOUT, "an axis pass gave up waiting for a staged tile copy; the field is not valid");
+}
+
 sfac_status sfac_plan_set_wait_limit(sfac_plan* plan, long long wait_cycles, int hold) {
     if (!plan || wait_cycles < 1) return fail(SFAC_EINVAL, "need a plan and wait_cycles >= 1");
     plan->wait_cycles = wait_cycles;
@@ -418,15 +440,10 @@ sfac_status sfac_plan_check(sfac_plan* plan, void* stream) {
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    unsigned int word = 0;
-    cudaError_t err = cudaMemcpyAsync(&word, plan->status, sizeof(word), cudaMemcpyDeviceToHost, st);
+    cudaError_t err = cudaMemcpyAsync(plan->status_host, plan->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) return cuda_fail(err, "status read");
-    if (word == 0) return SFAC_OK;
-    err = cudaMemsetAsync(plan->status, 0, sizeof(word), st);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
-    if (err != cudaSuccess) return cuda_fail(err, "status reset");
-    return fail(SFAC_ETIMEOUT, "an axis pass gave up waiting for a staged tile copy; the field is not valid");
+    return status_after_sync(plan, st);
 }
 
 sfac_status sfac_diagnostics(sfac_plan* plan, const void* u_dev, double* out, void* stream) {
@@ -500,9 +517,12 @@ sfac_status sfac_step_host(sfac_plan* plan, void* u_host, long long nsteps, void
     if (s != SFAC_OK) return s;
     err = cudaMemcpyAsync(u_host, plan->staging, bytes, cudaMemcpyDeviceToHost, st);
     if (err != cudaSuccess) return cuda_fail(err, "device-to-host copy");
+    // the status word rides along: one synchronisation for both
+    err = cudaMemcpyAsync(plan->status_host, plan->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+    if (err != cudaSuccess) return cuda_fail(err, "status read");
     err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) return cuda_fail(err, "stream synchronise");
-    return sfac_plan_check(plan, stream);
+    return status_after_sync(plan, st);
 }
 
 }  // extern "C"
