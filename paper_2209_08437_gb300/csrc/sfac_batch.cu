@@ -43,9 +43,17 @@ const BatchConfig kConfigs[] = {
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
-cudaError_t setup_batch(int prec, const BatchConfig& c, int sms, int* grid) {
-    return prec == SFAC_FP64 ? sfac::setup_batch_f64(c.wpb, c.es, sms, grid)
-                             : sfac::setup_batch_f32(c.wpb, c.es, sms, grid);
+// Strided items of 256+ points are staged in shared memory (FP32, 8-warp
+// shapes of >= 2 groups, which run one CTA per SM anyway: smaller CTAs would
+// lose resident CTAs to the buffers); the launch provides the buffers only if
+// some instance has such a pass.
+int stage_of(int prec, const BatchConfig& c, bool long_strided) {
+    return (prec == SFAC_FP32 && c.wpb == 8 && c.mult >= 2 && long_strided) ? c.mult : 0;
+}
+
+cudaError_t setup_batch(int prec, const BatchConfig& c, int stage, int sms, int* grid) {
+    return prec == SFAC_FP64 ? sfac::setup_batch_f64(c.wpb, c.es, 0, sms, grid)
+                             : sfac::setup_batch_f32(c.wpb, c.es, stage, sms, grid);
 }
 
 cudaError_t dispatch_batch(int prec, const BatchConfig& c, int grid, const sfac::BatchSchedule& sc, cudaStream_t s) {
@@ -283,7 +291,11 @@ sfac_status build_schedule(sfac_batch* B, cudaStream_t st) {
     sc.spin_limit = B->spin_limit;
     sc.hold_instance = B->hold_instance;
     sc.common = B->dev_common;
-    cudaError_t err = setup_batch(B->prec, c, B->sms, &B->grid);
+    bool long_strided = false;
+    for (const sfac::BatchInst& I : B->inst)
+        for (int a = 1; a < I.dim; ++a) long_strided = long_strided || I.n[a] >= 256;
+    sc.stage = stage_of(B->prec, c, long_strided);
+    cudaError_t err = setup_batch(B->prec, c, sc.stage, B->sms, &B->grid);
     if (err != cudaSuccess) return bcuda(err, "batch kernel setup");
     B->prepared = true;
     return SFAC_OK;

@@ -83,6 +83,32 @@ __device__ __noinline__ void batch_lines(const PassArgs& pa, bool strided, long 
     line.template store<E>(x, t);
 }
 
+// One warp-group of a staged strided item: its lines sit line by line in the
+// warp's staging buffer `stage` (line stride S complex values), group m.
+template <typename R, int N, int E>
+__device__ __noinline__ void batch_lines_staged(const PassArgs& pa, C2<R>* stage, int S, int m, C2<R>* region,
+                                                int lane) {
+    constexpr int T = N / E;
+    constexpr int LPW = 32 / T;
+    using Ex = WarpExchange<R, N, E>;
+    const int j = lane / T, t = lane % T;
+    C2<R>* line = stage + (m * LPW + j) * S;
+    const Ex ex{region + j * Ex::LINE_ELEMS};
+    C2<R> x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = line[t + e * T];
+    fused_pass<R, N, E, false>(x, t, pa, ex);
+#pragma unroll
+    for (int e = 0; e < E; ++e) line[t + e * T] = x[e];
+}
+
+// Bytes of dynamic shared memory of one launch.
+template <typename R>
+__host__ __device__ constexpr size_t batch_smem_bytes(int wpb, int stage) {
+    return sizeof(C2<R>) * ((size_t)wpb * BATCH_REGION + BATCH_COMMON_ELEMS +
+                            (stage > 0 ? (size_t)wpb * batch_stage_elems(stage) : 0));
+}
+
 // Launched with blockDim.x = 32 * (warps per CTA) <= MAXT and dynamic shared
 // memory for BATCH_REGION complex values per warp plus BATCH_COMMON_ELEMS;
 // MINB CTAs per SM must fit the register allocation.
@@ -98,6 +124,8 @@ batch_kernel(const BatchSchedule b) {
     const C2<R>* gcommon = static_cast<const C2<R>*>(b.common);
     for (int i = threadIdx.x; i < BATCH_COMMON_ELEMS; i += blockDim.x) common[i] = gcommon[i];
     __syncthreads();
+    // This warp's staging buffer for strided items (b.stage > 0, FP32).
+    C2<R>* stage = common + BATCH_COMMON_ELEMS + (b.stage > 0 ? warp * batch_stage_elems(b.stage) : 0);
     int p = 0;  // phase of the last item: claimed items increase, so p only moves forward
     for (;;) {
         unsigned long long item = 0;
@@ -162,6 +190,54 @@ batch_kernel(const BatchSchedule b) {
 
         const int lpw = 32 * batch_elems<ES>(N) / N;
         const bool strided = a > 0;
+        // Staged strided item: its L = mult * lpw lines are adjacent column
+        // pairs of one slab (the slab's pair count is a multiple of L, so no
+        // item straddles slabs or is partial). The warp copies the N rows of
+        // those 2L columns into its staging buffer with 16-byte loads, runs
+        // each warp-group from there and writes the block back with 16-byte
+        // stores: one L2 round trip per item, in whole 32-byte sectors, instead
+        // of one per group at 8 or 16 bytes a row.
+        bool staged = false;
+        if constexpr (sizeof(R) == 4) {
+            const int L = b.mult * lpw;
+            const long long pairs = inner / 2;
+            // Only lines of 256+ points: their groups read 8 or 16 bytes a row;
+            // shorter lines already read whole sectors and gain nothing.
+            staged = b.stage > 0 && strided && N >= 256 && b.mult == b.stage && pairs % L == 0;
+            if (staged) {
+                const int S = N + BATCH_STAGE_PAD;
+                const long long first = g * L;                  // first line of the item
+                const long long o = first / pairs;
+                R* base = static_cast<R*>(I.u) + o * (long long)N * inner + 2 * (first - o * pairs);
+                const int q4 = L / 2;                           // 16-byte pieces per row (a power of two)
+                const int qs = __ffs(q4) - 1;
+                for (int f = lane; f < N * q4; f += 32) {
+                    const int k = f >> qs, q = f & (q4 - 1);
+                    const float4 v = __ldcg(reinterpret_cast<const float4*>(base + (long long)k * inner) + q);
+                    stage[(2 * q) * S + k] = C2<R>{R(v.x), R(v.y)};
+                    stage[(2 * q + 1) * S + k] = C2<R>{R(v.z), R(v.w)};
+                }
+                __syncwarp();
+                for (int m = 0; m < b.mult; ++m) {
+                    switch (N) {
+                        case 32: batch_lines_staged<R, 32, ES>(pa, stage, S, m, region, lane); break;
+                        case 64: batch_lines_staged<R, 64, ES>(pa, stage, S, m, region, lane); break;
+                        case 128: batch_lines_staged<R, 128, ES>(pa, stage, S, m, region, lane); break;
+                        case 256: batch_lines_staged<R, 256, ES>(pa, stage, S, m, region, lane); break;
+                        default: batch_lines_staged<R, 512, 16>(pa, stage, S, m, region, lane); break;
+                    }
+                    __syncwarp();
+                }
+                for (int f = lane; f < N * q4; f += 32) {
+                    const int k = f >> qs, q = f & (q4 - 1);
+                    const C2<R> lo = stage[(2 * q) * S + k], hi = stage[(2 * q + 1) * S + k];
+                    reinterpret_cast<float4*>(base + (long long)k * inner)[q] =
+                        make_float4(float(lo.x), float(lo.y), float(hi.x), float(hi.y));
+                }
+                __syncwarp();
+            }
+        }
+        if (!staged) {
         for (int m = 0; m < b.mult; ++m) {
             const long long first = (g * b.mult + m) * lpw;
             if (first >= pa.clines) break;
@@ -173,6 +249,7 @@ batch_kernel(const BatchSchedule b) {
                 default: batch_lines<R, 512, 16>(pa, strided, first, region, lane); break;
             }
             __syncwarp();
+        }
         }
         // Publish: the stores above happen before the count is raised.
         if (lane == 0) {
@@ -197,13 +274,12 @@ constexpr int batch_small_minb() {
 }
 
 template <typename R, int ES>
-cudaError_t setup_batch(int wpb, int sms, int* grid) {
-    if (wpb < 1 || wpb > 8) return cudaErrorInvalidValue;
+cudaError_t setup_batch(int wpb, int stage, int sms, int* grid) {
+    if (wpb < 1 || wpb > 8 || stage < 0 || stage > 4) return cudaErrorInvalidValue;
     auto kern = wpb <= 4 ? batch_kernel<R, ES, 128, batch_small_minb<R>()> : batch_kernel<R, ES, 256, 1>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(sizeof(C2<R>) * (8 * BATCH_REGION + BATCH_COMMON_ELEMS)));
+    const size_t smem = batch_smem_bytes<R>(wpb, stage);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    const size_t smem = sizeof(C2<R>) * ((size_t)wpb * BATCH_REGION + BATCH_COMMON_ELEMS);
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
     if (err != cudaSuccess) return err;
@@ -215,7 +291,7 @@ cudaError_t setup_batch(int wpb, int sms, int* grid) {
 template <typename R, int ES>
 cudaError_t launch_batch(int wpb, int grid, const BatchSchedule& sc, cudaStream_t s) {
     if (wpb < 1 || wpb > 8 || grid < 1) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(C2<R>) * ((size_t)wpb * BATCH_REGION + BATCH_COMMON_ELEMS);
+    const size_t smem = batch_smem_bytes<R>(wpb, sc.stage);
     if (wpb <= 4)
         batch_kernel<R, ES, 128, batch_small_minb<R>()><<<grid, wpb * 32, smem, s>>>(sc);
     else

@@ -7,9 +7,9 @@
 #include "sfac_batch.cuh"
 
 namespace sfac {
-cudaError_t setup_batch_f32(int wpb, int es, int sms, int* grid) {
-    if (es == 16) return setup_batch<float, 16>(wpb, sms, grid);
-    if (es == 8) return setup_batch<float, 8>(wpb, sms, grid);
+cudaError_t setup_batch_f32(int wpb, int es, int stage, int sms, int* grid) {
+    if (es == 16) return setup_batch<float, 16>(wpb, stage, sms, grid);
+    if (es == 8) return setup_batch<float, 8>(wpb, stage, sms, grid);
     return cudaErrorInvalidValue;
 }
 cudaError_t launch_batch_f32(int wpb, int es, int grid, const BatchSchedule& sc, cudaStream_t s) {

@@ -2,9 +2,10 @@
 #include "sfac_batch.cuh"
 
 namespace sfac {
-cudaError_t setup_batch_f64(int wpb, int es, int sms, int* grid) {
+cudaError_t setup_batch_f64(int wpb, int es, int stage, int sms, int* grid) {
     (void)es;
-    return setup_batch<double, 16>(wpb, sms, grid);
+    (void)stage;  // FP64 items are not staged
+    return setup_batch<double, 16>(wpb, 0, sms, grid);
 }
 cudaError_t launch_batch_f64(int wpb, int es, int grid, const BatchSchedule& sc, cudaStream_t s) {
     (void)es;

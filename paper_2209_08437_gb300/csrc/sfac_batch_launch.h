@@ -39,7 +39,14 @@ struct BatchSchedule {
     long long spin_limit;          // polls before a wait gives up
     int hold_instance;             // test hook: this instance's second pass never becomes ready (-1: off)
     const void* common;            // twiddles and twists of every length (batch_common_offset), precision R
+    int stage;                     // > 0: strided items are staged in shared memory (= mult; FP32 only)
 };
+
+// Staging buffer of one warp for strided items (see sfac_batch.cuh), in
+// complex values: the item's lines (mult * 32/T of them, 512 * mult values for
+// 16 values per thread) with BATCH_STAGE_PAD values of padding each.
+constexpr int BATCH_STAGE_PAD = 2;
+__host__ __device__ constexpr int batch_stage_elems(int mult) { return 544 * mult; }
 
 // Twiddles e^{-2 pi i k/N} and twists e^{i pi k/N} depend on the line length
 // only. One device block holds them for N = 32 .. 512, as complex values of the
@@ -56,10 +63,12 @@ constexpr int SFAC_BATCH_TIMEOUT = 1;
 // The persistent batch kernel with `wpb` warps per CTA (<= 8) and `es` values
 // per thread for lines up to 256 points (8 or 16; FP64 always 16).
 // setup_*: set its shared-memory limit and compute the persistent grid for
-// `sms` SMs (call outside stream capture). launch_*: enqueue it on `s`.
+// `sms` SMs with staging buffers for `stage` warp-groups per item (0: none);
+// call outside stream capture. launch_*: enqueue it on `s` (staging as in
+// sc.stage, which must equal the `stage` given to setup).
 // cudaErrorInvalidValue for other shapes.
-cudaError_t setup_batch_f32(int wpb, int es, int sms, int* grid);
-cudaError_t setup_batch_f64(int wpb, int es, int sms, int* grid);
+cudaError_t setup_batch_f32(int wpb, int es, int stage, int sms, int* grid);
+cudaError_t setup_batch_f64(int wpb, int es, int stage, int sms, int* grid);
 cudaError_t launch_batch_f32(int wpb, int es, int grid, const BatchSchedule& sc, cudaStream_t s);
 cudaError_t launch_batch_f64(int wpb, int es, int grid, const BatchSchedule& sc, cudaStream_t s);
 

@@ -306,8 +306,13 @@ sfac_status sfac_server_round(sfac_server* S, long long chunk, int shape, void* 
     S->sc.spin_limit = S->spin_limit;
     S->sc.hold_instance = -1;
     S->sc.common = S->dev_common;
-    cudaError_t err = S->prec == SFAC_FP64 ? sfac::setup_batch_f64(wpb, es, S->sms, &S->grid)
-                                           : sfac::setup_batch_f32(wpb, es, S->sms, &S->grid);
+    // strided passes of 256+ points in this round: stage them (see sfac_batch.cuh)
+    bool long_strided = false;
+    for (const sfac::BatchInst& I : inst)
+        for (int a = 1; a < I.dim; ++a) long_strided = long_strided || I.n[a] >= 256;
+    S->sc.stage = (S->prec == SFAC_FP32 && wpb == 8 && mult >= 2 && long_strided) ? mult : 0;
+    cudaError_t err = S->prec == SFAC_FP64 ? sfac::setup_batch_f64(wpb, es, 0, S->sms, &S->grid)
+                                           : sfac::setup_batch_f32(wpb, es, S->sc.stage, S->sms, &S->grid);
     if (err == cudaSuccess)
         err = cudaMemsetAsync(S->scratch, 0, sizeof(unsigned long long) * (S->slots.size() + 2), st);
     if (err == cudaSuccess)
