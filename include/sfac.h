@@ -195,9 +195,11 @@ sfac_status sfac_plan_tables(const sfac_params* params, int axis, double* lambda
 typedef struct sfac_batch sfac_batch;
 
 /* Build a batch: params[i] describes instance i (dim 2 or 3; every n[l] a power
- * of two in [32, 512]; one precision for all). FP64 tables per instance and
- * axis are computed on the host (as in sfac_plan_create) and uploaded once on
- * `stream` (synchronised). SFAC_EUNSUPPORTED for other shapes. */
+ * of two in [32, 512]; one precision for all). The spectral factors of each
+ * instance and axis are computed in FP64 on the host (as in sfac_plan_create);
+ * the twists and twiddles, which depend on the line length only, are held once
+ * per batch for every length. Both are uploaded on `stream` (synchronised).
+ * SFAC_EUNSUPPORTED for other shapes. */
 sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream, sfac_batch** out);
 
 /* Release the batch (synchronises the device first). NULL is a no-op. */
@@ -269,8 +271,9 @@ sfac_status sfac_batch_launch_noalloc(sfac_batch* batch, void* stream);
 /* ------------------------------------------------------------------------ */
 
 /* A server owns one device arena of `arena_bytes`. An admitted request gets a
- * slot whose field and per-axis tables (as in sfac_plan_create) stay resident in
- * the arena until its result is fetched. A round advances every active slot by
+ * slot whose field and per-axis spectral factors (as in sfac_plan_create) stay
+ * resident in the arena until its result is fetched; twists and twiddles are
+ * held once per server for every line length. A round advances every active slot by
  * up to `chunk` steps in one persistent launch of the batched kernel, so
  * requests admitted while a round runs join the next round. A slot always
  * advances in whole chunks counted from its own first step, so its result does
@@ -284,7 +287,8 @@ sfac_status sfac_server_create(size_t arena_bytes, int max_slots, int prec, void
 /* Release everything (synchronises the device first). NULL is a no-op. */
 sfac_status sfac_server_destroy(sfac_server* server);
 
-/* Arena bytes one request with these parameters occupies (field + tables). */
+/* Arena bytes one request with these parameters occupies (field + the two
+ * spectral factors per axis). */
 sfac_status sfac_server_request_bytes(const sfac_params* params, size_t* bytes);
 
 /* Admit a request: dim 2 or 3, every n[l] a power of two in [32, 512], the
