@@ -349,6 +349,69 @@ def test_second_order_in_time_and_local_defect():
     assert np.all(np.abs(ratios - 8.0) < 0.8), ratios
 
 
+# ------------------------------------------------------------- energy -------
+
+def _ginzburg_landau_energy(u, n, eps, a, b):
+    """h_1...h_d (1/4 sum (u^2-1)^2 + eps^2/2 sum over grid edges ((u_i - u_j)/h_l)^2),
+    the edges to the zero Dirichlet boundary included: the classical discrete
+    Ginzburg-Landau energy, written with differences rather than a matrix."""
+    hs = [(b - a) / (m + 1) for m in n]
+    grad = 0.0
+    for l, h in enumerate(hs):
+        ax = u.ndim - 1 - l
+        pad = [(0, 0)] * u.ndim
+        pad[ax] = (1, 1)
+        grad += np.sum(np.diff(np.pad(u, pad), axis=ax) ** 2) / h ** 2
+    return float(np.prod(hs)) * (0.25 * np.sum((u * u - 1) ** 2) + 0.5 * eps ** 2 * grad)
+
+
+@pytest.mark.parametrize("n", [(5, 7), (3, 4, 6), (9,)], ids=str)
+def test_energy_alpha2_is_ginzburg_landau(n):
+    """Example 5's energy E(u) = h^d((1/4)(u^2-1)^T(u^2-1) - (1/2) u^T A u): with
+    alpha = 2 on every axis B_l is the Dirichlet Laplacian times eps^2, so E is
+    the edge-difference sum above. Non-square grids (a different h per axis) make
+    an axis mix-up fail too."""
+    sch = O.Scheme(n, (2.0,) * len(n), 0.3, 0.01, -1.0, 1.0)
+    u = np.random.default_rng(len(n)).uniform(-1.0, 1.0, tuple(reversed(n)))
+    ref = _ginzburg_landau_energy(u, n, 0.3, -1.0, 1.0)
+    assert abs(O.discrete_energy(u, sch) - ref) <= 1e-13 * ref
+
+
+@pytest.mark.parametrize("alpha", [(1.2, 1.8), (1.5, 1.05), (1.95, 1.3)], ids=str)
+def test_energy_bounds_and_zero_field(alpha):
+    """For alpha in (1, 2), B is symmetric with a negative diagonal and
+    nonpositive row sums (Proposition 1), so -u^T A u >= 0 (Gershgorin) and
+    E(u) >= h^d (1/4) sum (u^2-1)^2; E(0) = h^d N / 4 exactly; at u = +-1 E is
+    the nonlocal term alone, which grows with eps^2."""
+    n = (11, 6)
+    hs = [2.0 / (m + 1) for m in n]
+    sch = O.Scheme(n, alpha, 0.2, 0.01)
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        u = rng.uniform(-1.0, 1.0, (6, 11))
+        bulk = float(np.prod(hs)) * 0.25 * np.sum((u * u - 1) ** 2)
+        assert O.discrete_energy(u, sch) > bulk
+    assert O.discrete_energy(np.zeros((6, 11)), sch) == pytest.approx(np.prod(hs) * 66 / 4, rel=1e-15)
+    ones = np.ones((6, 11))
+    e1 = O.discrete_energy(ones, sch)
+    e2 = O.discrete_energy(ones, O.Scheme(n, alpha, 0.4, 0.01))
+    assert e1 > 0 and e2 == pytest.approx(4 * e1, rel=1e-13)
+
+
+def test_energy_decays_along_the_scheme():
+    """Example 5 reports that E(u^n) decreases monotonically; on a 31 x 31 grid
+    with u0 = 0.8 rand - 0.4 it does so over 200 steps."""
+    p = I.Problem(n=(31, 31), alpha=(1.5, 1.7), eps=0.05, tau=0.01)
+    sch = O.Scheme.for_problem(p)
+    u = I.random_field(p, 4, -0.4, 0.4)
+    prev = O.discrete_energy(u, sch)
+    for _ in range(200):
+        u = sch.step(u)
+        e = O.discrete_energy(u, sch)
+        assert e < prev
+        prev = e
+
+
 # ------------------------------------------------- planted mistakes --------
 
 class _Mutant:
@@ -396,3 +459,29 @@ def test_planted_mistakes_fail_table2(mutant):
     with _Mutant(*mutant):
         et = _table2_first_two_level()
     assert not _close_to_printed(et, 1.2824e-7), et
+
+
+def _energy_mutant(sign=-0.5, bulk=0.25, hpow=True):
+    def energy(u, scheme):
+        Au = np.zeros_like(u)
+        hprod = 1.0
+        for ax in range(u.ndim):
+            h = (scheme.b - scheme.a) / (scheme.n[ax] + 1)
+            hprod = hprod * h if hpow else h
+            Au += O.apply_axis(u, O.matrix_B(scheme.alpha[ax], scheme.eps, h, scheme.n[ax]), ax + 1)
+        w = u * u - 1.0
+        return hprod * (bulk * float(np.sum(w * w)) + sign * float(np.sum(u * Au)))
+    return energy
+
+
+@pytest.mark.parametrize("mutant", [_energy_mutant(sign=+0.5), _energy_mutant(bulk=0.5),
+                                    _energy_mutant(hpow=False)],
+                         ids=["energy-sign", "energy-bulk-weight", "energy-h-power"])
+def test_planted_mistakes_fail_energy_pins(mutant):
+    n = (5, 7)
+    sch = O.Scheme(n, (2.0, 2.0), 0.3, 0.01)
+    u = np.random.default_rng(2).uniform(-1.0, 1.0, (7, 5))
+    with _Mutant("discrete_energy", mutant):
+        got = O.discrete_energy(u, sch)
+    ref = _ginzburg_landau_energy(u, n, 0.3, -1.0, 1.0)
+    assert abs(got - ref) > 1e-6 * ref
