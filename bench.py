@@ -11,7 +11,7 @@ the field resident in HBM; the FP32 path is measured the same way and
 reported under "paths". Each timed step is preceded by an L2 flush (a 256 MiB
 write) and timed alone with CUDA events on the launching stream.
 
-  python bench.py [--steps K] [--warmup W] [--workload 2d1024|2d64|3d256]
+  python bench.py [--steps K] [--warmup W] [--workload 2d1024|2d64|3d256|3d512]
   python bench.py --impl reference      # the CPU FP64 oracle on the host cores
 """
 from __future__ import annotations
@@ -36,6 +36,8 @@ import sfac_inputs as I  # noqa: E402
 METRIC = "point-steps/s FP32 vs FP64 path at stated err vs oracle; served p50/p99 latency"
 UNIT = "point-steps/s"
 
+PROBE_3D512 = I.Problem(n=(512, 512, 512), alpha=(1.2, 1.5, 1.8), eps=0.08, tau=2e-3)
+
 WORKLOADS = {
     "2d1024": dict(problem=I.CONFIG2, u0=I.config2_u0,
                    name="2D SFAC n=1024^2 (1,048,576 unknowns), alpha=(1.3,1.7), eps=0.05, tau=1e-3, "
@@ -45,6 +47,10 @@ WORKLOADS = {
     "3d256": dict(problem=I.CONFIG3, u0=I.config3_u0,
                   name="3D SFAC n=256^3 (16,777,216 unknowns), alpha=(1.2,1.5,1.8), eps=0.08, tau=2e-3, "
                        "u0~U[-1,1] seed 2"),
+    # HBM probe: fields of 0.5 GB (FP32) and 1.07 GB (FP64), far above the 129 MB L2.
+    "3d512": dict(problem=PROBE_3D512, u0=lambda: I.random_field(PROBE_3D512, 2, -1.0, 1.0),
+                  name="3D SFAC n=512^3 (134,217,728 unknowns; HBM probe), alpha=(1.2,1.5,1.8), eps=0.08, "
+                       "tau=2e-3, u0~U[-1,1] seed 2"),
 }
 
 # Algorithmic work of one fused axis pass per real unknown: six complex FFTs of
