@@ -507,7 +507,8 @@ def main():
     e2e = time_e2e(S, torch, problem, u0, S.SFAC_FP64, max(3, min(args.steps, 10)))
     e2e["value"] *= world
     parity = parity_check(S, torch, problem, u0, args.parity_steps) if args.parity_steps > 0 else None
-    cpu = None if args.no_cpu_baseline else cpu_baseline(problem, u0)
+    # the oracle's CPU baseline is timed at N = 1 only
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(problem, u0)
 
     line = {
         "metric": METRIC, "value": value64, "unit": UNIT, "n_gpus": world, "steps": args.steps,
