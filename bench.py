@@ -75,12 +75,9 @@ FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.07e9 / 1e12
 #       python bench.py --steps 2 --warmup 3 [--workload 3d256] --parity-steps 0 --no-cpu-baseline
 # (profiles/axis_pass_dram_traffic.md). A key must be removed when its kernel changes.
 NCU_TRAFFIC = {
-    ("2d1024", "f64", 0): 8583936, ("2d1024", "f64", 1): 8603136,
     ("2d1024", "f32", 0): 4284598, ("2d1024", "f32", 1): 4285513,
-    ("3d256", "f64", 0): 204113971, ("3d256", "f64", 1): 209806540, ("3d256", "f64", 2): 209815552,
     ("3d256", "f32", 0): 72380342, ("3d256", "f32", 1): 75123309, ("3d256", "f32", 2): 75733504,
     # 3d512: -k regex:axis_pass -s 15 -c 15 (the FP64 single-pass timings and the FP32 warm-up steps)
-    ("3d512", "f64", 0): 2086881280, ("3d512", "f64", 1): 2091721600, ("3d512", "f64", 2): 2092453632,
     ("3d512", "f32", 0): 1008508672, ("3d512", "f32", 1): 1014830250, ("3d512", "f32", 2): 1014986837,
 }
 

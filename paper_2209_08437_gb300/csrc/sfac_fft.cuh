@@ -213,4 +213,175 @@ __device__ __forceinline__ void line_fft(C2<R> (&x)[E], int t, const C2<R>* __re
     FftPass<R, N, E, 1, INV>::run(x, t, tw, ex);
 }
 
+// ---------------------------------------------------------------------------
+// FP64 passes with ratio twiddles (FP64 lines of up to 1024 points, radix 8/4/2).
+//
+// The FP64 passes are bound by the FP64 pipe, so what counts is the number of
+// FP64 instructions. A twiddle w = c + i s is stored as c and the ratio
+// rho = s / c: w a = c t with t = (1 + i rho) a, two FMAs instead of the four
+// instructions of a complex product. The scale c is not applied on its own: it
+// rides in the FMA of the butterfly that consumes the product
+// (u + c t = fma(c, t, u)). Where both operands of a butterfly carry a scale
+// (c_a t_a +- c_b t_b), the butterfly computes t_a +- (c_b / c_a) t_b and hands
+// c_a on to the next butterfly. This is the same arithmetic rewritten around
+// FMAs; each rounding stays relative to the values it rounds, also for large
+// rho (c near 0 multiplies the large t back down in one FMA).
+//
+// Records, per pass of span P > 1 and radix RAD, one per k in [0, P), in pass
+// order; c_r + i s_r = e^{-2 pi i r k / (P RAD)}, rho_r = s_r / c_r:
+//   RAD 8 (16 values): rho_1..rho_7, c_4, c_6/c_2, c_5/c_1, c_7/c_3, c_3/c_1,
+//                      c_2, c_1, c_1/sqrt 2, 0
+//   RAD 4 (8 values):  rho_1, rho_2, rho_3, c_2, c_3/c_1, c_1, 0, 0
+//   RAD 2 (2 values):  rho_1, c_1
+// Pass P = 1 has no twiddles and no records.
+
+__device__ __forceinline__ C2<double> cfma_d(double s, C2<double> u, C2<double> e) {
+    return {fma(s, u.x, e.x), fma(s, u.y, e.y)};
+}
+// (1 -+ i rho) a (forward: w = c (1 + i rho); inverse: conj(w) = c (1 - i rho))
+template <bool INV>
+__device__ __forceinline__ C2<double> ratio_mul(C2<double> a, double rho) {
+    return INV ? C2<double>{fma(rho, a.y, a.x), fma(-rho, a.x, a.y)}
+               : C2<double>{fma(-rho, a.y, a.x), fma(rho, a.x, a.y)};
+}
+// v e^{-+ i pi / 2}
+template <bool INV>
+__device__ __forceinline__ C2<double> rot_quarter(C2<double> v) {
+    return INV ? C2<double>{-v.y, v.x} : C2<double>{v.y, -v.x};
+}
+// v e^{-+ i pi / 4} = u / sqrt 2 and v e^{-+ 3 i pi / 4} = u / sqrt 2: the u
+template <bool INV>
+__device__ __forceinline__ C2<double> rot_eighth_u(C2<double> v) {
+    return INV ? C2<double>{v.x - v.y, v.x + v.y} : C2<double>{v.x + v.y, v.y - v.x};
+}
+template <bool INV>
+__device__ __forceinline__ C2<double> rot_3eighth_u(C2<double> v) {
+    return INV ? C2<double>{-(v.x + v.y), v.x - v.y} : C2<double>{v.y - v.x, -(v.x + v.y)};
+}
+
+__device__ __forceinline__ double2 ld_rec2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+
+// a_r <- sum_r w_r a_r e^{-+2 pi i r s / 8} with the twiddles of record p: the
+// radix-2 decimation of Dft<double, 8>, scales carried as described above.
+template <bool INV>
+__device__ __forceinline__ void dft8_ratio(C2<double> (&a)[8], const double* __restrict__ p) {
+    const double2 p01 = ld_rec2(p), p23 = ld_rec2(p + 2), p45 = ld_rec2(p + 4), p67 = ld_rec2(p + 6);
+    const double2 p89 = ld_rec2(p + 8), pab = ld_rec2(p + 10), pcd = ld_rec2(p + 12), pef = ld_rec2(p + 14);
+    const C2<double> t1 = ratio_mul<INV>(a[1], p01.x), t2 = ratio_mul<INV>(a[2], p01.y);
+    const C2<double> t3 = ratio_mul<INV>(a[3], p23.x), t4 = ratio_mul<INV>(a[4], p23.y);
+    const C2<double> t5 = ratio_mul<INV>(a[5], p45.x), t6 = ratio_mul<INV>(a[6], p45.y);
+    const C2<double> t7 = ratio_mul<INV>(a[7], p67.x);
+    const double c4 = p67.y, q62 = p89.x, q51 = p89.y, q73 = pab.x, q31 = pab.y;
+    const double c2 = pcd.x, c1 = pcd.y, c1r = pef.x;
+    // first stage: pairs (r, r + 4); the pairs other than (0, 4) keep a scale
+    const C2<double> l0p = cfma_d(c4, t4, a[0]), l0m = cfma_d(-c4, t4, a[0]);
+    const C2<double> l2p = cfma_d(q62, t6, t2), l2m = cfma_d(-q62, t6, t2);  // x c_2
+    const C2<double> l1p = cfma_d(q51, t5, t1), l1m = cfma_d(-q51, t5, t1);  // x c_1
+    const C2<double> l3p = cfma_d(q73, t7, t3), l3m = cfma_d(-q73, t7, t3);  // x c_3
+    // second stage, even half: scale 1
+    const C2<double> r2 = rot_quarter<INV>(l2m);
+    const C2<double> e0 = cfma_d(c2, l2p, l0p), e2 = cfma_d(-c2, l2p, l0p);
+    const C2<double> e1 = cfma_d(c2, r2, l0m), e3 = cfma_d(-c2, r2, l0m);
+    // second stage, odd half: x c_1
+    const C2<double> r3 = rot_quarter<INV>(l3m);
+    const C2<double> o0 = cfma_d(q31, l3p, l1p), o2 = cfma_d(-q31, l3p, l1p);
+    const C2<double> o1 = cfma_d(q31, r3, l1m), o3 = cfma_d(-q31, r3, l1m);
+    // third stage
+    a[0] = cfma_d(c1, o0, e0);
+    a[4] = cfma_d(-c1, o0, e0);
+    const C2<double> u1 = rot_eighth_u<INV>(o1);
+    a[1] = cfma_d(c1r, u1, e1);
+    a[5] = cfma_d(-c1r, u1, e1);
+    const C2<double> v2 = rot_quarter<INV>(o2);
+    a[2] = cfma_d(c1, v2, e2);
+    a[6] = cfma_d(-c1, v2, e2);
+    const C2<double> u3 = rot_3eighth_u<INV>(o3);
+    a[3] = cfma_d(c1r, u3, e3);
+    a[7] = cfma_d(-c1r, u3, e3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4_ratio(C2<double> (&a)[4], const double* __restrict__ p) {
+    const double2 p01 = ld_rec2(p), p23 = ld_rec2(p + 2), p45 = ld_rec2(p + 4);
+    const C2<double> t1 = ratio_mul<INV>(a[1], p01.x), t2 = ratio_mul<INV>(a[2], p01.y);
+    const C2<double> t3 = ratio_mul<INV>(a[3], p23.x);
+    const double c2 = p23.y, q31 = p45.x, c1 = p45.y;
+    const C2<double> ep = cfma_d(c2, t2, a[0]), em = cfma_d(-c2, t2, a[0]);
+    const C2<double> op = cfma_d(q31, t3, t1), om = cfma_d(-q31, t3, t1);  // x c_1
+    const C2<double> r = rot_quarter<INV>(om);
+    a[0] = cfma_d(c1, op, ep);
+    a[2] = cfma_d(-c1, op, ep);
+    a[1] = cfma_d(c1, r, em);
+    a[3] = cfma_d(-c1, r, em);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2_ratio(C2<double> (&a)[2], const double* __restrict__ p) {
+    const double2 rc = ld_rec2(p);
+    const C2<double> t1 = ratio_mul<INV>(a[1], rc.x);
+    const C2<double> a0 = a[0];
+    a[0] = cfma_d(rc.y, t1, a0);
+    a[1] = cfma_d(-rc.y, t1, a0);
+}
+
+// Doubles per record of a radix-RAD pass.
+constexpr int ratio_record(int rad) { return rad == 8 ? 16 : (rad == 4 ? 8 : 2); }
+
+// The Stockham passes of FftPass with ratio twiddles (double, radix 2/4/8).
+// OFF: offset of this pass's records in the table.
+template <int N, int E, int P, int OFF, bool INV>
+struct FftPassRatio {
+    static constexpr int RAD = (P * E <= N) ? E : (N / P);
+    static constexpr bool LAST = (P * RAD == N);
+    static constexpr int T = N / E;
+    static constexpr int Q = E / RAD;
+    static constexpr int REC = ratio_record(RAD);
+    static constexpr int NEXT_OFF = OFF + (P > 1 ? P * REC : 0);
+    static_assert(RAD == 2 || RAD == 4 || RAD == 8, "ratio twiddles: radix 2, 4 or 8");
+
+    template <class Ex>
+    static __device__ __forceinline__ void run(C2<double> (&x)[E], int t, const double* __restrict__ rt,
+                                               const Ex& ex) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int i = t + q * T;
+            const int k = i & (P - 1);
+            C2<double> a[RAD];
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) a[r] = x[q + r * Q];
+            if constexpr (P == 1) {
+                Dft<double, RAD, INV>::run(a);
+            } else {
+                const double* rec = rt + OFF + k * REC;
+                if constexpr (RAD == 8) dft8_ratio<INV>(a, rec);
+                else if constexpr (RAD == 4) dft4_ratio<INV>(a, rec);
+                else dft2_ratio<INV>(a, rec);
+            }
+            if constexpr (LAST) {
+#pragma unroll
+                for (int r = 0; r < RAD; ++r) x[q + r * Q] = a[r];
+            } else {
+                const int j = (i - k) * RAD + k;
+#pragma unroll
+                for (int r = 0; r < RAD; ++r) ex.put(j + r * P, a[r]);
+            }
+        }
+        if constexpr (!LAST) {
+            Ex::sync();
+#pragma unroll
+            for (int e = 0; e < E; ++e) x[e] = ex.get(t + e * T);
+            Ex::sync();
+            FftPassRatio<N, E, P * RAD, NEXT_OFF, INV>::run(x, t, rt, ex);
+        }
+    }
+};
+
+// Unnormalised FFT of one FP64 line with ratio twiddles (table `rt`, records as
+// described above for this N and E).
+template <int N, int E, bool INV, class Ex>
+__device__ __forceinline__ void line_fft_ratio(C2<double> (&x)[E], int t, const double* __restrict__ rt,
+                                               const Ex& ex) {
+    FftPassRatio<N, E, 1, 0, INV>::run(x, t, rt, ex);
+}
+
 }  // namespace sfac

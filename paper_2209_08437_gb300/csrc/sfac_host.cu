@@ -236,4 +236,42 @@ void compute_axis(double alpha, double eps, double tau, double a, double b, int 
 }
 
 
+
+// Ratio twiddles (sfac_fft.cuh, FftPassRatio). For pass span P and radix RAD:
+// c_r + i s_r = e^{-2 pi i r k / (P RAD)}. A cosine that is exactly 0 (w = -+i)
+// is stored as 2^-60 with rho = s / 2^-60 exact: c t then equals s times the
+// other part to within 2^-60 of |a|, far below the rounding of the sums.
+std::vector<double> ratio_twiddles(int N, int E) {
+    std::vector<double> out;
+    for (int P = 1; P < N;) {
+        const int RAD = (P * E <= N) ? E : N / P;
+        if (P > 1) {
+            for (int k = 0; k < P; ++k) {
+                double c[8] = {}, s[8] = {}, rho[8] = {};
+                for (int r = 0; r < RAD; ++r) {
+                    double cv, sv;
+                    sincospi_frac(2LL * r * k, (long long)P * RAD, &cv, &sv);
+                    c[r] = cv == 0.0 ? std::ldexp(1.0, -60) : cv;
+                    s[r] = -sv;
+                    rho[r] = s[r] / c[r];
+                }
+                if (RAD == 8) {
+                    const double rec[16] = {rho[1], rho[2], rho[3], rho[4], rho[5], rho[6], rho[7], c[4],
+                                            c[6] / c[2], c[5] / c[1], c[7] / c[3], c[3] / c[1],
+                                            c[2], c[1], (double)((long double)c[1] * sqrtl(0.5L)), 0.0};
+                    out.insert(out.end(), rec, rec + 16);
+                } else if (RAD == 4) {
+                    const double rec[8] = {rho[1], rho[2], rho[3], c[2], c[3] / c[1], c[1], 0.0, 0.0};
+                    out.insert(out.end(), rec, rec + 8);
+                } else {
+                    out.push_back(rho[1]);
+                    out.push_back(c[1]);
+                }
+            }
+        }
+        P *= RAD;
+    }
+    return out;
+}
+
 }  // namespace sfac

@@ -26,6 +26,8 @@ void set_last_error(const std::string& msg);
 //   increments the FP32 passes add; see sfac_pass.cuh)
 //  twist  = N complex e^{i pi k / N} (interleaved re, im)
 //  twid   = N complex e^{-2 pi i m / N}
+//  rtwid  = FP64 passes with E <= 8 values per thread: the ratio-twiddle
+//           records of the FFT passes (sfac_fft.cuh, FftPassRatio)
 // J^Q_s(v) = v / sqrt(E + (1 - E) v^2) with E = e^{-2 s} is applied to every
 // value on load when jq_in != 0 and on store when jq_out != 0.
 struct PassArgs {
@@ -38,6 +40,7 @@ struct PassArgs {
     const void* eS;
     const void* twist;
     const void* twid;
+    const void* rtwid = nullptr;
     double jq_in_E, jq_in_1mE;
     double jq_out_E, jq_out_1mE;
     int jq_in, jq_out;
@@ -52,6 +55,10 @@ struct PassArgs {
 };
 
 constexpr unsigned int SFAC_PASS_TIMEOUT = 1u;
+
+// Values per thread of the FP64 CTA pass for FFT length N. Lengths up to 1024
+// (E <= 8) run their FFTs with ratio twiddles.
+constexpr int f64_elems_per_thread(int N) { return N >= 2048 ? 16 : (N < 8 ? N : 8); }
 
 // Launch one pass for line length N (a power of two in [4, 4096]).
 // Returns cudaErrorInvalidValue for an unsupported N.

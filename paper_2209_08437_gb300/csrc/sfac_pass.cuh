@@ -94,6 +94,30 @@ __device__ __forceinline__ void apply_spectral(C2<R> (&x)[E], int t, const C2<R>
     line_fft<R, N, E, true>(x, t, tw, ex);
 }
 
+// The same with the FFTs on ratio twiddles (FP64, E <= 8; table rt).
+template <int N, int E, class Ex>
+__device__ __forceinline__ void apply_spectral_ratio(C2<double> (&x)[E], int t, const double* __restrict__ rt,
+                                                     const Ex& ex, const double* __restrict__ m) {
+    constexpr int T = N / E;
+    line_fft_ratio<N, E, false>(x, t, rt, ex);
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = cscale(x[e], m[t + e * T]);
+    line_fft_ratio<N, E, true>(x, t, rt, ex);
+}
+
+// Twiddle source of the FP64 chain: the complex table, or (RATIO) the
+// ratio-twiddle records.
+template <typename R, int N, int E, bool RATIO>
+struct Spectral {
+    const C2<R>* __restrict__ tw;
+    const double* __restrict__ rt;
+    template <class Ex>
+    __device__ __forceinline__ void apply(C2<R> (&x)[E], int t, const Ex& ex, const R* __restrict__ m) const {
+        if constexpr (RATIO) apply_spectral_ratio<N, E>(x, t, rt, ex, m);
+        else apply_spectral<R, N, E>(x, t, tw, ex, m);
+    }
+};
+
 // Zero the values at positions >= nmem (the padding of a zero-padded pass).
 template <typename R, int N, int E>
 __device__ __forceinline__ void zero_tail(C2<R> (&x)[E], int t, int nmem) {
@@ -106,29 +130,30 @@ __device__ __forceinline__ void zero_tail(C2<R> (&x)[E], int t, int nmem) {
 // e^{tau/2 C} e^{tau S} e^{tau/2 C} on the line held in x (FP64 passes; the
 // tables hold e^{t lambda} / N). PADDED: three zero-padded linear convolutions
 // with real multipliers, no twist.
-template <typename R, int N, int E, bool PADDED, class Ex>
+template <typename R, int N, int E, bool PADDED, bool RATIO, class Ex>
 __device__ __forceinline__ void two_level_chain(C2<R> (&x)[E], int t, const PassArgs& a, const Ex& ex) {
     constexpr int T = N / E;
-    const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
+    static_assert(!RATIO || (sizeof(R) == 8 && E <= 8), "ratio twiddles: FP64, E <= 8");
+    const Spectral<R, N, E, RATIO> sp{static_cast<const C2<R>*>(a.twid), static_cast<const double*>(a.rtwid)};
     if constexpr (PADDED) {
-        apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eC));
+        sp.apply(x, t, ex, static_cast<const R*>(a.eC));
         zero_tail<R, N, E>(x, t, a.nmem);
-        apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eS));
+        sp.apply(x, t, ex, static_cast<const R*>(a.eS));
         zero_tail<R, N, E>(x, t, a.nmem);
-        apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eC));
+        sp.apply(x, t, ex, static_cast<const R*>(a.eC));
         return;
     }
     const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
     // e^{tau/2 C}
-    apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eC));
+    sp.apply(x, t, ex, static_cast<const R*>(a.eC));
     // e^{tau S} = Theta^{-1} F^{-1} e^{tau Lambda_S} F Theta
 #pragma unroll
     for (int e = 0; e < E; ++e) x[e] = cmul(x[e], ldg_c2(twist + t + e * T));
-    apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eS));
+    sp.apply(x, t, ex, static_cast<const R*>(a.eS));
 #pragma unroll
     for (int e = 0; e < E; ++e) x[e] = cmulc(x[e], ldg_c2(twist + t + e * T));
     // e^{tau/2 C}
-    apply_spectral<R, N, E>(x, t, tw, ex, static_cast<const R*>(a.eC));
+    sp.apply(x, t, ex, static_cast<const R*>(a.eC));
 }
 
 // For lines of up to SFAC_ROLLED_MAX_N points the FP32 chain runs rolled: one
@@ -275,14 +300,15 @@ __device__ __forceinline__ void two_level_pass_incr(C2<R> (&x0)[E], int t, const
     for (int e = 0; e < E; ++e) x0[e] = cadd(x0[e], d[e]);
 }
 
-// One whole pass on the line held in x: FP32 in increment form, FP64 plain.
-template <typename R, int N, int E, bool PADDED, class Ex>
+// One whole pass on the line held in x: FP32 in increment form, FP64 plain
+// (RATIO: FFTs on the ratio twiddles of a.rtwid).
+template <typename R, int N, int E, bool PADDED, bool RATIO = false, class Ex>
 __device__ __forceinline__ void fused_pass(C2<R> (&x)[E], int t, const PassArgs& a, const Ex& ex) {
     if constexpr (sizeof(R) == 4) {
         two_level_pass_incr<R, N, E, PADDED>(x, t, a, ex);
     } else {
         if (a.jq_in) jq_all<R, E>(x, a.jq_in_E, a.jq_in_1mE);
-        two_level_chain<R, N, E, PADDED>(x, t, a, ex);
+        two_level_chain<R, N, E, PADDED, RATIO>(x, t, a, ex);
         if (a.jq_out) jq_all<R, E>(x, a.jq_out_E, a.jq_out_1mE);
     }
 }
@@ -516,7 +542,7 @@ axis_pass_kernel(const PassArgs a) {
 
     C2<R> x[E];
     line.template load<E>(x, t);
-    fused_pass<R, N, E, PADDED>(x, t, a, ex);
+    fused_pass<R, N, E, PADDED, (sizeof(R) == 8 && E <= 8)>(x, t, a, ex);
     line.template store<E>(x, t);
 }
 
@@ -691,6 +717,8 @@ template <typename R, int N, bool PADDED>
 cudaError_t launch_n(const PassArgs& a, cudaStream_t s) {
     constexpr int E = elems_per_thread<N>();
     constexpr int T = N / E;
+    // the host builds the FP64 ratio-twiddle records for this E
+    static_assert(sizeof(R) != 8 || E == f64_elems_per_thread(N), "FP64 values per thread");
     if constexpr (sizeof(R) == 4 && N >= 32 && N <= 512) {
         // FP32: warp-local lines with 16 values per thread. Two warps per CTA
         // for long lines (few lines: many small CTAs spread better over 152

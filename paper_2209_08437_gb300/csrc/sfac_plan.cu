@@ -78,6 +78,7 @@ struct sfac_plan {
         const void* eS;
         const void* twist;
         const void* twid;
+        const void* rtwid;  // FP64 ratio twiddles (E <= 8), else NULL
         int fft_len;  // N of the pass: n, or the padded length L
         bool padded;
         // FP64 diagnostic tables: lambda/N, mu/N, twist, twiddles (padded axes:
@@ -130,6 +131,7 @@ sfac_status launch_axis(sfac_plan* P, void* u, int ax, int jq_in, int jq_out, cu
     a.eS = P->ax[ax].eS;
     a.twist = P->ax[ax].twist;
     a.twid = P->ax[ax].twid;
+    a.rtwid = P->ax[ax].rtwid;
     a.jq_in = jq_in != 0;
     a.jq_in_E = jq_in == 2 ? P->jq_full_E : P->jq_half_E;
     a.jq_in_1mE = jq_in == 2 ? P->jq_full_1mE : P->jq_half_1mE;
@@ -239,17 +241,33 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
         delete P;
         return cuda_fail(err, "cudaGetDevice");
     }
-    // One device block: per axis eC[n], eS[n], twist[2n], twid[2n] reals.
+    // FP64 ratio twiddles of each axis's FFT length (passes with E <= 8).
+    std::vector<double> rtw[3];
+    if (params->prec == SFAC_FP64) {
+        try {
+            for (int l = 0; l < params->dim; ++l) {
+                const int N = padded[l] ? pad[l].L : params->n[l];
+                const int E = sfac::f64_elems_per_thread(N);
+                if (E <= 8) rtw[l] = sfac::ratio_twiddles(N, E);
+            }
+        } catch (const std::bad_alloc&) {
+            delete P;
+            return fail(SFAC_ENOMEM, "host allocation failed");
+        }
+    }
+    // One device block: per axis eC[n], eS[n], twist[2n], twid[2n] reals, the
+    // FP64 diagnostic tables, and the ratio twiddles.
     const size_t rs = real_size(P);
-    size_t off[3][8], total = 0;
+    size_t off[3][9], total = 0;
     long long max_partials = 1;
     {
         long long inner = 1;
         for (int l = 0; l < params->dim; ++l) {
             const size_t n = padded[l] ? (size_t)pad[l].L : (size_t)params->n[l];
-            const size_t sz[8] = {n * rs, n * rs, padded[l] ? 0 : 2 * n * rs, 2 * n * rs,
-                                  n * 8,  padded[l] ? 0 : n * 8, padded[l] ? 0 : 2 * n * 8, 2 * n * 8};
-            for (int q = 0; q < 8; ++q) {
+            const size_t sz[9] = {n * rs, n * rs, padded[l] ? 0 : 2 * n * rs, 2 * n * rs,
+                                  n * 8,  padded[l] ? 0 : n * 8, padded[l] ? 0 : 2 * n * 8, 2 * n * 8,
+                                  rtw[l].size() * sizeof(double)};
+            for (int q = 0; q < 9; ++q) {
                 off[l][q] = total;
                 total += align256(sz[q]);
             }
@@ -300,6 +318,8 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
         for (int q = 0; q < 4; ++q)
             if (!dsrc[q]->empty())
                 std::memcpy(blob.data() + off[l][4 + q], dsrc[q]->data(), dsrc[q]->size() * sizeof(double));
+        if (!rtw[l].empty())
+            std::memcpy(blob.data() + off[l][8], rtw[l].data(), rtw[l].size() * sizeof(double));
         for (int q = 0; q < 4; ++q) {
             unsigned char* dst = blob.data() + off[l][q];
             const std::vector<double>& v = *src[q];
@@ -331,6 +351,7 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
         P->ax[l].eS = base + off[l][1];
         P->ax[l].twist = padded[l] ? nullptr : base + off[l][2];
         P->ax[l].twid = base + off[l][3];
+        P->ax[l].rtwid = rtw[l].empty() ? nullptr : base + off[l][8];
         P->ax[l].padded = padded[l];
         P->ax[l].fft_len = padded[l] ? pad[l].L : params->n[l];
         P->ax[l].dA = reinterpret_cast<const double*>(base + off[l][4]);
