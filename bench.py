@@ -75,6 +75,8 @@ FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.07e9 / 1e12
 #       python bench.py --steps 2 --warmup 3 [--workload 3d256] --parity-steps 0 --no-cpu-baseline
 # (profiles/axis_pass_dram_traffic.md). A key must be removed when its kernel changes.
 NCU_TRAFFIC = {
+    # 2d1024 FP64: -k regex:axis_pass -s 6 -c 2 (the two passes of the first timed step)
+    ("2d1024", "f64", 0): 8592128, ("2d1024", "f64", 1): 8580864,
     ("2d1024", "f32", 0): 4284598, ("2d1024", "f32", 1): 4285513,
     ("3d256", "f32", 0): 72380342, ("3d256", "f32", 1): 75123309, ("3d256", "f32", 2): 75733504,
     # 3d512: -k regex:axis_pass -s 15 -c 15 (the FP64 single-pass timings and the FP32 warm-up steps)
