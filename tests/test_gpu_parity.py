@@ -31,7 +31,7 @@ def gpu_run(prob, u0, nsteps, prec=S.SFAC_FP64):
 
 
 SHAPES_2D = [(4, 4), (4, 8), (8, 4), (16, 16), (64, 32), (32, 128), (256, 256), (1024, 8),
-             (8, 1024), (2048, 4), (4, 4096)]
+             (8, 1024), (2048, 4), (4, 4096), (512, 16), (16, 512)]
 SHAPES_3D = [(4, 4, 4), (4, 8, 16), (32, 4, 8), (16, 16, 16), (64, 8, 32)]
 
 
