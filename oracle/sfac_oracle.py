@@ -43,7 +43,7 @@ Axis l of the paper is numpy axis d - l.
 Every function is pinned by a test in tests/test_oracle_pins.py against
 something the paper or mathematics fixes (Proposition 1, the stencil of
 eq. (disFAC), the alpha = 2 Laplacian, library expm, the Bernoulli ODE, the
-printed numbers of Tables 2 and 4, the maximum principle, order 2, and for the
+printed numbers of Tables 1, 2 and 4, the maximum principle, order 2, and for the
 energy of Example 5 the alpha = 2 Ginzburg-Landau edge sum).
 """
 from __future__ import annotations

