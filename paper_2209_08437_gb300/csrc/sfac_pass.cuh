@@ -24,6 +24,9 @@
 //  - the TMA-staged kernel of sfac_pass_staged_f32.cu (FP32 strided axes) and
 //    the batch kernel of sfac_batch.cuh run the same warp-local lines.
 // The FP32 chain is the increment form, rolled for N <= SFAC_ROLLED_MAX_N.
+// The FP64 CTA kernel runs its FFTs on ratio twiddles for N <= 1024 (E <= 8;
+// FftPassRatio in sfac_fft.cuh, records in PassArgs::rtwid); the batch kernel
+// and lines of 2048+ points use the complex twiddle table.
 #pragma once
 
 #include <atomic>
