@@ -1,8 +1,8 @@
 // Host check of the device FFT core (csrc/sfac_fft.cuh): the register-resident
 // Stockham FFT of one line, run by T = N / E host threads that meet at a
 // barrier wherever the CTA would synchronise, against a long-double DFT.
-//  - complex twiddles, FP64 (E as the FP64 kernels) and FP32 (E = 16, scalar
-//    arithmetic: the packed FP32 instructions exist on the GPU only);
+//  - complex twiddles, FP64 (E as the FP64 kernels) and FP32 (E = 16, on the
+//    packed two-lane FP32 forms, emulated lane by lane by the host shim);
 //  - ratio twiddles (FP64, E <= 8) with the table of ratio_twiddles; the table
 //    is followed by poison values, so a record read past its end shows up as
 //    a wrong result.

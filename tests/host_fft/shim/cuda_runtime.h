@@ -9,6 +9,10 @@
 struct double2 { double x, y; };
 struct float2 { float x, y; };
 inline float2 make_float2(float a, float b) { return {a, b}; }
+// The packed two-lane FP32 operations: each lane rounds as the scalar operation.
+inline float2 __fadd2_rn(float2 a, float2 b) { return {a.x + b.x, a.y + b.y}; }
+inline float2 __fmul2_rn(float2 a, float2 b) { return {a.x * b.x, a.y * b.y}; }
+inline float2 __ffma2_rn(float2 a, float2 b, float2 c) { return {std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y)}; }
 typedef int cudaError_t;
 typedef void* cudaStream_t;
 using std::fma;

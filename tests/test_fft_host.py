@@ -3,7 +3,8 @@ host thread per GPU thread, meeting at a barrier wherever the CTA synchronises
 (tests/host_fft/check_fft.cpp). Every line length 4..2048 of the FP64 passes,
 forward and inverse, with complex twiddles and (E <= 8) with the ratio
 twiddles of the FP64 plan passes, and the FP32 radix-16 structure of lengths
-32..2048 (scalar arithmetic), against a long-double DFT.
+32..2048 on the packed two-lane FP32 forms the kernels use (emulated lane by
+lane), against a long-double DFT.
 
 Bound: the error of a radix-2-based FFT grows like log2 N roundings, so the
 max error relative to the largest exact value must stay below 4 log2(N) u
@@ -27,7 +28,7 @@ def results(tmp_path_factory):
     if cxx is None:
         pytest.skip("no host C++ compiler")
     exe = str(tmp_path_factory.mktemp("fft") / "check_fft")
-    cmd = [cxx, "-std=c++20", "-O2", "-DSFAC_PACKED_F32=0", "-I", os.path.join(HERE, "shim"), "-I", CSRC,
+    cmd = [cxx, "-std=c++20", "-O2", "-ffp-contract=off", "-I", os.path.join(HERE, "shim"), "-I", CSRC,
            "-x", "c++", os.path.join(CSRC, "sfac_host.cu"), os.path.join(HERE, "check_fft.cpp"),
            "-o", exe, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
