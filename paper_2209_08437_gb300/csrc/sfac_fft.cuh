@@ -225,7 +225,11 @@ __device__ __forceinline__ void line_fft(C2<R> (&x)[E], int t, const C2<R>* __re
 // (c_a t_a +- c_b t_b), the butterfly computes t_a +- (c_b / c_a) t_b and hands
 // c_a on to the next butterfly. This is the same arithmetic rewritten around
 // FMAs; each rounding stays relative to the values it rounds, also for large
-// rho (c near 0 multiplies the large t back down in one FMA).
+// rho (c near 0 multiplies the large t back down in one FMA). Twiddles stored
+// as a cosine and a ratio so that products fold into multiply-adds are the
+// idea of FMA-oriented FFT kernels (Linzer and Feig, IEEE Trans. Signal
+// Process. 1993; Goedecker, SIAM J. Sci. Comput. 1997); the scale bookkeeping
+// through the three radix-2 stages of the radix-8 butterfly is this file's.
 //
 // Records, per pass of span P > 1 and radix RAD, one per k in [0, P), in pass
 // order; c_r + i s_r = e^{-2 pi i r k / (P RAD)}, rho_r = s_r / c_r:
