@@ -347,7 +347,7 @@ int batch_device(const sfac_batch* B) { return B->device; }
 
 extern "C" {
 
-sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream, sfac_batch** out) {
+sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream, sfac_batch** out) try {
     if (!out) return bfail(SFAC_EINVAL, "out is NULL");
     *out = nullptr;
     if (!params || count < 1) return bfail(SFAC_EINVAL, "need params and count >= 1");
@@ -453,9 +453,11 @@ sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream
     B->nsteps.assign(count, 0);
     *out = B;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_batch_destroy(sfac_batch* B) {
+sfac_status sfac_batch_destroy(sfac_batch* B) try {
     if (!B) return SFAC_OK;
     int prev = -1;
     cudaGetDevice(&prev);
@@ -469,9 +471,11 @@ sfac_status sfac_batch_destroy(sfac_batch* B) {
     if (prev >= 0 && prev != B->device) cudaSetDevice(prev);
     delete B;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_batch_prepare(sfac_batch* B, void* const* u_dev, const long long* nsteps, void* stream) {
+sfac_status sfac_batch_prepare(sfac_batch* B, void* const* u_dev, const long long* nsteps, void* stream) try {
     if (!B || !u_dev || !nsteps) return bfail(SFAC_EINVAL, "NULL argument");
     for (int i = 0; i < B->count; ++i) {
         if (!u_dev[i]) return bfail(SFAC_EINVAL, "field " + std::to_string(i) + " is NULL");
@@ -481,31 +485,39 @@ sfac_status sfac_batch_prepare(sfac_batch* B, void* const* u_dev, const long lon
         B->nsteps[i] = nsteps[i];
     }
     return build_schedule(B, static_cast<cudaStream_t>(stream));
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_batch_launch(sfac_batch* B, void* stream) {
+sfac_status sfac_batch_launch(sfac_batch* B, void* stream) try {
     if (!B) return bfail(SFAC_EINVAL, "batch is NULL");
     return launch(B, static_cast<cudaStream_t>(stream));
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_batch_wait(sfac_batch* B, void* stream) {
+sfac_status sfac_batch_wait(sfac_batch* B, void* stream) try {
     if (!B) return bfail(SFAC_EINVAL, "batch is NULL");
     cudaError_t err = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (err != cudaSuccess) return bcuda(err, "batch synchronise");
     if (*B->host_error == sfac::SFAC_BATCH_TIMEOUT) return bfail(SFAC_ETIMEOUT, "a dependency wait gave up");
     if (*B->host_error != 0) return bfail(SFAC_ECUDA, "batch kernel reported an error");
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_batch_step(sfac_batch* B, void* const* u_dev, const long long* nsteps, void* stream) {
+sfac_status sfac_batch_step(sfac_batch* B, void* const* u_dev, const long long* nsteps, void* stream) try {
     sfac_status st = sfac_batch_prepare(B, u_dev, nsteps, stream);
     if (st != SFAC_OK) return st;
     st = sfac_batch_launch(B, stream);
     if (st != SFAC_OK) return st;
     return sfac_batch_wait(B, stream);
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_batch_autotune(sfac_batch* B, int max_steps, void* stream, int* choice) {
+sfac_status sfac_batch_autotune(sfac_batch* B, int max_steps, void* stream, int* choice) try {
     if (!B || max_steps < 1) return bfail(SFAC_EINVAL, "need a batch and max_steps >= 1");
     if (!B->prepared) return bfail(SFAC_EINVAL, "prepare the batch with its fields first");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -566,17 +578,21 @@ sfac_status sfac_batch_autotune(sfac_batch* B, int max_steps, void* stream, int*
     if (result != SFAC_OK) return result;
     if (choice) *choice = best_cfg;
     return rebuilt;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_batch_set_config(sfac_batch* B, int config) {
+sfac_status sfac_batch_set_config(sfac_batch* B, int config) try {
     if (!B || config < 0 || config >= kNumConfigs) return bfail(SFAC_EINVAL, "bad batch or config index");
     B->config = config;
     B->prepared = false;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
 sfac_status sfac_batch_get_config(const sfac_batch* B, int* config, int* warps_per_cta, int* values_per_thread,
-                                  int* groups_per_item) {
+                                  int* groups_per_item) try {
     if (!B) return bfail(SFAC_EINVAL, "batch is NULL");
     const BatchConfig& c = kConfigs[B->config];
     if (config) *config = B->config;
@@ -584,17 +600,21 @@ sfac_status sfac_batch_get_config(const sfac_batch* B, int* config, int* warps_p
     if (values_per_thread) *values_per_thread = c.es;
     if (groups_per_item) *groups_per_item = c.mult;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
 int sfac_batch_num_configs(void) { return kNumConfigs; }
 
-sfac_status sfac_batch_set_wait_limit(sfac_batch* B, long long spin_limit, int hold_instance) {
+sfac_status sfac_batch_set_wait_limit(sfac_batch* B, long long spin_limit, int hold_instance) try {
     if (!B || spin_limit < 1 || hold_instance < -1 || hold_instance >= B->count)
         return bfail(SFAC_EINVAL, "bad batch, limit or instance");
     B->spin_limit = spin_limit;
     B->hold_instance = hold_instance;
     B->prepared = false;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
 }  // extern "C"

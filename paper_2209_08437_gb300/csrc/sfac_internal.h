@@ -6,10 +6,17 @@
 
 #include <string>
 
+#include "sfac.h"
+
 namespace sfac {
 
 // Record the message returned by sfac_last_error() for the calling thread.
 void set_last_error(const std::string& msg);
+
+// Status of a C ABI entry point whose body threw: called from the entry
+// point's catch handler, it records a message and returns SFAC_ENOMEM (host
+// memory, threads or other host resources ran out). No exception leaves the ABI.
+sfac_status abi_exception_status() noexcept;
 
 // Arguments of one fused axis pass over the field (see sfac_pass.cuh).
 //

@@ -76,7 +76,7 @@ int batch_device(const sfac_batch* batch);
 
 extern "C" {
 
-sfac_status sfac_batch_launch_noalloc(sfac_batch* batch, void* stream) {
+sfac_status sfac_batch_launch_noalloc(sfac_batch* batch, void* stream) try {
     if (!batch) return nfail(SFAC_EINVAL, "batch is NULL");
     const int count = sfac::batch_count(batch);
     if (count > kMaxInstances)
@@ -91,6 +91,8 @@ sfac_status sfac_batch_launch_noalloc(sfac_batch* batch, void* stream) {
     if (st == SFAC_OK) st = sfac::batch_launch_with_scratch(batch, scratch, static_cast<cudaStream_t>(stream));
     if (prev != dev) cudaSetDevice(prev);
     return st;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
 }  // extern "C"

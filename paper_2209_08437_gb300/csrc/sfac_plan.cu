@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <string>
 #include <vector>
@@ -32,6 +33,23 @@ sfac_status fail(sfac_status st, const std::string& msg) {
 
 namespace sfac {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+sfac_status abi_exception_status() noexcept {
+    const char* what = "host resource error";
+    try {
+        throw;
+    } catch (const std::bad_alloc&) {
+        what = "host allocation failed";
+    } catch (const std::exception& e) {
+        what = e.what();
+    } catch (...) {
+    }
+    try {
+        g_last_error = what;
+    } catch (...) {
+    }
+    return SFAC_ENOMEM;
+}
 }  // namespace sfac
 
 namespace {
@@ -179,7 +197,7 @@ int sfac_version(void) { return 100; }
 const char* sfac_last_error(void) { return g_last_error.c_str(); }
 
 sfac_status sfac_plan_tables(const sfac_params* params, int axis, double* lambda, double* mu,
-                             double* bcol, double* jq) {
+                             double* bcol, double* jq) try {
     sfac_status st = validate(params, false);
     if (st != SFAC_OK) return st;
     if (axis < 0 || axis >= params->dim) return fail(SFAC_EINVAL, "axis out of range");
@@ -200,9 +218,11 @@ sfac_status sfac_plan_tables(const sfac_params* params, int axis, double* lambda
         jq[3] = -std::expm1(-2.0 * params->tau);
     }
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan** out) {
+sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan** out) try {
     if (!out) return fail(SFAC_EINVAL, "out is NULL");
     *out = nullptr;
     sfac_status st = validate(params, true);
@@ -373,9 +393,11 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
     *P->status_host = 0;
     *out = P;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_plan_destroy(sfac_plan* plan) {
+sfac_status sfac_plan_destroy(sfac_plan* plan) try {
     if (!plan) return SFAC_OK;
     sfac_status st = SFAC_OK;
     {
@@ -388,9 +410,11 @@ sfac_status sfac_plan_destroy(sfac_plan* plan) {
     }
     delete plan;
     return st;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_step(sfac_plan* plan, void* u_dev, long long nsteps, void* stream) {
+sfac_status sfac_step(sfac_plan* plan, void* u_dev, long long nsteps, void* stream) try {
     if (!plan) return fail(SFAC_EINVAL, "plan is NULL");
     if (!u_dev) return fail(SFAC_EINVAL, "u_dev is NULL");
     if (nsteps < 0) return fail(SFAC_EINVAL, "nsteps must be >= 0");
@@ -399,9 +423,11 @@ sfac_status sfac_step(sfac_plan* plan, void* u_dev, long long nsteps, void* stre
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
     return run_steps(plan, u_dev, nsteps, static_cast<cudaStream_t>(stream));
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_axis_pass(sfac_plan* plan, void* u_dev, int axis, int jq_in, int jq_out, void* stream) {
+sfac_status sfac_axis_pass(sfac_plan* plan, void* u_dev, int axis, int jq_in, int jq_out, void* stream) try {
     if (!plan) return fail(SFAC_EINVAL, "plan is NULL");
     if (!u_dev) return fail(SFAC_EINVAL, "u_dev is NULL");
     if (axis < 0 || axis >= plan->p.dim) return fail(SFAC_EINVAL, "axis out of range");
@@ -410,16 +436,20 @@ sfac_status sfac_axis_pass(sfac_plan* plan, void* u_dev, int axis, int jq_in, in
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
     return launch_axis(plan, u_dev, axis, jq_in, jq_out, static_cast<cudaStream_t>(stream));
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_plan_info(const sfac_plan* plan, int axis, int* fft_len, int* padded) {
+sfac_status sfac_plan_info(const sfac_plan* plan, int axis, int* fft_len, int* padded) try {
     if (!plan || axis < 0 || axis >= plan->p.dim) return fail(SFAC_EINVAL, "bad plan or axis");
     if (fft_len) *fft_len = plan->ax[axis].fft_len;
     if (padded) *padded = plan->ax[axis].padded ? 1 : 0;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_plan_kernel(const sfac_plan* plan, int axis, const void* u_dev, int* kind) {
+sfac_status sfac_plan_kernel(const sfac_plan* plan, int axis, const void* u_dev, int* kind) try {
     if (!plan || axis < 0 || axis >= plan->p.dim || !kind) return fail(SFAC_EINVAL, "bad plan, axis or kind");
     long long inner = 1;
     for (int l = 0; l < axis; ++l) inner *= plan->p.n[l];
@@ -436,6 +466,8 @@ sfac_status sfac_plan_kernel(const sfac_plan* plan, int axis, const void* u_dev,
     else
         *kind = SFAC_KERNEL_CTA;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
 // The status word already copied to plan->status_host and the stream
@@ -449,14 +481,16 @@ static sfac_status status_after_sync(sfac_plan* plan, cudaStream_t st) {
     return fail(SFAC_ETIMEOUT, "an axis pass gave up waiting for a staged tile copy; the field is not valid");
 }
 
-sfac_status sfac_plan_set_wait_limit(sfac_plan* plan, long long wait_cycles, int hold) {
+sfac_status sfac_plan_set_wait_limit(sfac_plan* plan, long long wait_cycles, int hold) try {
     if (!plan || wait_cycles < 1) return fail(SFAC_EINVAL, "need a plan and wait_cycles >= 1");
     plan->wait_cycles = wait_cycles;
     plan->hold = hold != 0;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_plan_check(sfac_plan* plan, void* stream) {
+sfac_status sfac_plan_check(sfac_plan* plan, void* stream) try {
     if (!plan) return fail(SFAC_EINVAL, "plan is NULL");
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
@@ -465,9 +499,11 @@ sfac_status sfac_plan_check(sfac_plan* plan, void* stream) {
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) return cuda_fail(err, "status read");
     return status_after_sync(plan, st);
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_diagnostics(sfac_plan* plan, const void* u_dev, double* out, void* stream) {
+sfac_status sfac_diagnostics(sfac_plan* plan, const void* u_dev, double* out, void* stream) try {
     if (!plan || !u_dev || !out) return fail(SFAC_EINVAL, "NULL argument");
     if (reinterpret_cast<uintptr_t>(u_dev) % 16 != 0) return fail(SFAC_EINVAL, "u_dev must be 16-byte aligned");
     DeviceGuard g(plan->device);
@@ -504,18 +540,22 @@ sfac_status sfac_diagnostics(sfac_plan* plan, const void* u_dev, double* out, vo
     out[0] = host[2];                                 // max |u|
     out[1] = hprod * (0.25 * host[1] - 0.5 * host[0]);  // discrete energy
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_solve(sfac_plan* plan, void* u_dev, double T, void* stream) {
+sfac_status sfac_solve(sfac_plan* plan, void* u_dev, double T, void* stream) try {
     if (!plan) return fail(SFAC_EINVAL, "plan is NULL");
     if (!(std::isfinite(T) && T >= 0)) return fail(SFAC_EINVAL, "T must be finite and >= 0");
     const double q = T / plan->p.tau;
     const double r = std::nearbyint(q);
     if (std::fabs(q - r) > 1e-9 * std::fmax(1.0, q)) return fail(SFAC_EINVAL, "T is not a whole number of steps");
     return sfac_step(plan, u_dev, (long long)r, stream);
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_step_host(sfac_plan* plan, void* u_host, long long nsteps, void* stream) {
+sfac_status sfac_step_host(sfac_plan* plan, void* u_host, long long nsteps, void* stream) try {
     if (!plan) return fail(SFAC_EINVAL, "plan is NULL");
     if (!u_host) return fail(SFAC_EINVAL, "u_host is NULL");
     if (nsteps < 0) return fail(SFAC_EINVAL, "nsteps must be >= 0");
@@ -544,6 +584,8 @@ sfac_status sfac_step_host(sfac_plan* plan, void* u_host, long long nsteps, void
     err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) return cuda_fail(err, "stream synchronise");
     return status_after_sync(plan, st);
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
 }  // extern "C"

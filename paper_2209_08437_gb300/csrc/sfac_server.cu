@@ -141,7 +141,7 @@ struct sfac_server {
 
 extern "C" {
 
-sfac_status sfac_server_create(size_t arena_bytes, int max_slots, int prec, void* stream, sfac_server** out) {
+sfac_status sfac_server_create(size_t arena_bytes, int max_slots, int prec, void* stream, sfac_server** out) try {
     (void)stream;
     if (!out) return sfail(SFAC_EINVAL, "out is NULL");
     *out = nullptr;
@@ -174,9 +174,11 @@ sfac_status sfac_server_create(size_t arena_bytes, int max_slots, int prec, void
     S->slots.resize(max_slots);
     *out = S;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_server_destroy(sfac_server* S) {
+sfac_status sfac_server_destroy(sfac_server* S) try {
     if (!S) return SFAC_OK;
     cudaDeviceSynchronize();
     if (S->arena_mem) cudaFree(S->arena_mem);
@@ -187,18 +189,22 @@ sfac_status sfac_server_destroy(sfac_server* S) {
     if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
     delete S;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_server_request_bytes(const sfac_params* params, size_t* bytes) {
+sfac_status sfac_server_request_bytes(const sfac_params* params, size_t* bytes) try {
     if (!params || !bytes) return sfail(SFAC_EINVAL, "NULL argument");
     const sfac_status st = check_request(params, params->prec);
     if (st != SFAC_OK) return st;
     *bytes = request_bytes(*params);
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
 sfac_status sfac_server_admit(sfac_server* S, const sfac_params* params, const void* u0_host, long long nsteps,
-                              int* slot_out) {
+                              int* slot_out) try {
     if (!S || !u0_host || !slot_out) return sfail(SFAC_EINVAL, "NULL argument");
     *slot_out = -1;
     sfac_status st = check_request(params, S->prec);
@@ -220,8 +226,7 @@ sfac_status sfac_server_admit(sfac_server* S, const sfac_params* params, const v
     const size_t rs = real_bytes(p.prec);
     size_t pts = 1;
     for (int a = 0; a < p.dim; ++a) pts *= (size_t)p.n[a];
-    std::vector<unsigned char> blob(bytes, 0);
-    std::memcpy(blob.data(), u0_host, pts * rs);
+    std::vector<unsigned char> blob;
     Slot& s = S->slots[slot];
     s = Slot();
     s.inst.dim = p.dim;
@@ -229,6 +234,8 @@ sfac_status sfac_server_admit(sfac_server* S, const sfac_params* params, const v
     size_t cur = al256(pts * rs);
     unsigned char* base = static_cast<unsigned char*>(S->arena_mem) + off;
     try {
+        blob.assign(bytes, 0);
+        std::memcpy(blob.data(), u0_host, pts * rs);
         for (int a = 0; a < 3; ++a) {
             s.inst.n[a] = a < p.dim ? p.n[a] : 1;
             if (a >= p.dim) continue;
@@ -270,9 +277,11 @@ sfac_status sfac_server_admit(sfac_server* S, const sfac_params* params, const v
     s.done = 0;
     *slot_out = slot;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_server_round(sfac_server* S, long long chunk, int shape, void* stream) {
+sfac_status sfac_server_round(sfac_server* S, long long chunk, int shape, void* stream) try {
     if (!S || chunk < 1) return sfail(SFAC_EINVAL, "need a server and chunk >= 1");
     if (S->in_flight) return sfail(SFAC_EINVAL, "a round is already in flight (call sfac_server_wait)");
     int wpb = 0, es = 0, mult = 0;
@@ -325,9 +334,11 @@ sfac_status sfac_server_round(sfac_server* S, long long chunk, int shape, void* 
         return scuda(err, "round launch");
     }
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_server_wait(sfac_server* S, void* stream, int* finished, int max_finished, int* nfinished) {
+sfac_status sfac_server_wait(sfac_server* S, void* stream, int* finished, int max_finished, int* nfinished) try {
     if (!S || !nfinished || (max_finished > 0 && !finished)) return sfail(SFAC_EINVAL, "NULL argument");
     *nfinished = 0;
     if (!S->in_flight) return SFAC_OK;
@@ -347,9 +358,11 @@ sfac_status sfac_server_wait(sfac_server* S, void* stream, int* finished, int ma
     }
     *nfinished = nf;
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
-sfac_status sfac_server_fetch(sfac_server* S, int slot, void* u_host, int release) {
+sfac_status sfac_server_fetch(sfac_server* S, int slot, void* u_host, int release) try {
     if (!S || slot < 0 || slot >= (int)S->slots.size() || !S->slots[slot].used)
         return sfail(SFAC_EINVAL, "bad server or slot");
     Slot& s = S->slots[slot];
@@ -367,10 +380,12 @@ sfac_status sfac_server_fetch(sfac_server* S, int slot, void* u_host, int releas
         s = Slot();
     }
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
 sfac_status sfac_server_info(const sfac_server* S, size_t* free_bytes, size_t* largest_free, int* active,
-                             int* capacity) {
+                             int* capacity) try {
     if (!S) return sfail(SFAC_EINVAL, "server is NULL");
     if (free_bytes) *free_bytes = S->arena.total - S->arena.used;
     if (largest_free) *largest_free = S->arena.largest_free();
@@ -379,6 +394,8 @@ sfac_status sfac_server_info(const sfac_server* S, size_t* free_bytes, size_t* l
     if (active) *active = n;
     if (capacity) *capacity = (int)S->slots.size();
     return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
 }
 
 }  // extern "C"
