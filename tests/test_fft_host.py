@@ -29,6 +29,7 @@ def results(tmp_path_factory):
         pytest.skip("no host C++ compiler")
     exe = str(tmp_path_factory.mktemp("fft") / "check_fft")
     cmd = [cxx, "-std=c++20", "-O2", "-ffp-contract=off", "-I", os.path.join(HERE, "shim"), "-I", CSRC,
+           "-I", os.path.join(ROOT, "include"),
            "-x", "c++", os.path.join(CSRC, "sfac_host.cu"), os.path.join(HERE, "check_fft.cpp"),
            "-o", exe, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
