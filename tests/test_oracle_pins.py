@@ -394,6 +394,132 @@ def test_second_order_in_time_and_local_defect():
     assert np.all(np.abs(ratios - 8.0) < 0.8), ratios
 
 
+# ------------------------------------------------ axis assignment (d >= 2) ---
+#
+# Eq. (2DA) writes A = I (x) B_{alpha_1} + B_{alpha_2} (x) I for the vector u
+# ordered with x^(1) fastest (the ordering under eq. (condition)), and eq. (3DA)
+# the three-term sum; eq. (newlinear) splits C_alpha and S_alpha the same way.
+# The pins below build those Kronecker sums literally with np.kron on grids whose
+# axes differ in n (hence in h) and in alpha, so that every assignment of alpha,
+# h or the memory axis to the wrong paper axis changes the result.
+
+_AXIS_CASES = [((2, 3), (1.2, 1.8)), ((3, 3), (1.15, 1.85)), ((4, 3), (1.7, 1.3)),
+               ((2, 3, 4), (1.2, 1.5, 1.8)), ((3, 2, 2), (1.9, 1.1, 1.45))]
+
+
+def _kron_sum(mats):
+    """sum_l I (x) .. (x) M_l (x) .. (x) I with M_1 acting on the fastest index:
+    the paper's M_d (x) ... (x) M_1 ordering of eqs. (2DA), (3DA), (newlinear)."""
+    sizes = [m.shape[0] for m in mats]
+    total = np.zeros((int(np.prod(sizes)),) * 2)
+    for l, M in enumerate(mats):
+        term = np.eye(1)
+        for k in reversed(range(len(mats))):  # axis d first (slowest)
+            term = np.kron(term, M if k == l else np.eye(sizes[k]))
+        total += term
+    return total
+
+
+def _axis_pieces(n, alpha, eps, a, b):
+    Bs, Cs, Ss = [], [], []
+    for nl, al in zip(n, alpha):
+        h = (b - a) / (nl + 1)
+        B = O.matrix_B(al, eps, h, nl)
+        C, S = O.split_CS(B)
+        Bs.append(B)
+        Cs.append(C)
+        Ss.append(S)
+    return Bs, Cs, Ss
+
+
+def _kron_two_level_step(n, alpha, eps, tau, a, b, u):
+    """J^Q_{tau/2} e^{tau/2 C_alpha} e^{tau S_alpha} e^{tau/2 C_alpha} J^Q_{tau/2} u
+    with C_alpha, S_alpha the full Kronecker sums of eq. (newlinear) and dense
+    matrix exponentials of the whole (prod n) x (prod n) matrices."""
+    _, Cs, Ss = _axis_pieces(n, alpha, eps, a, b)
+    Ca, Sa = _kron_sum(Cs), _kron_sum(Ss)
+    EC = scipy.linalg.expm(0.5 * tau * Ca)
+    ES = scipy.linalg.expm(tau * Sa)
+    E = math.exp(-tau)
+    jq = lambda v: v / np.sqrt(v * v + (1 - v * v) * E)
+    v = jq(u.ravel())  # C order of shape (n_d, .., n_1): x^(1) fastest
+    return jq(EC @ (ES @ (EC @ v))).reshape(u.shape)
+
+
+def _kron_one_level_step(n, alpha, eps, tau, a, b, u):
+    """J^Q_{tau/2} e^{tau A} J^Q_{tau/2} u with A from eq. (2DA) / (3DA)."""
+    Bs, _, _ = _axis_pieces(n, alpha, eps, a, b)
+    EA = scipy.linalg.expm(tau * _kron_sum(Bs))
+    E = math.exp(-tau)
+    jq = lambda v: v / np.sqrt(v * v + (1 - v * v) * E)
+    return jq(EA @ jq(u.ravel())).reshape(u.shape)
+
+
+def _axis_assignment_errors(n, alpha, eps=0.3, tau=0.2, a=-1.0, b=1.5):
+    """Largest differences of one oracle step (two-level and one-level) and of the
+    oracle energy from the Kronecker-sum definitions. A mutant that makes the
+    oracle fail to run at all counts as an infinite error."""
+    u = np.random.default_rng(sum(n)).uniform(-1.0, 1.0, tuple(reversed(n)))
+    try:
+        two = O.Scheme(n, alpha, eps, tau, a, b).step(u)
+        one = O.Scheme(n, alpha, eps, tau, a, b, kind="one_level").step(u)
+        en = O.discrete_energy(u, O.Scheme(n, alpha, eps, tau, a, b))
+    except (ValueError, IndexError):
+        return math.inf, math.inf, math.inf
+    e_two = float(np.abs(two - _kron_two_level_step(n, alpha, eps, tau, a, b, u)).max())
+    e_one = float(np.abs(one - _kron_one_level_step(n, alpha, eps, tau, a, b, u)).max())
+    Bs, _, _ = _axis_pieces(n, alpha, eps, a, b)
+    hprod = float(np.prod([(b - a) / (nl + 1) for nl in n]))
+    v = u.ravel()
+    ref = hprod * (0.25 * float(np.sum((v * v - 1) ** 2)) - 0.5 * float(v @ (_kron_sum(Bs) @ v)))
+    return e_two, e_one, abs(en - ref) / abs(ref)
+
+
+@pytest.mark.parametrize("n,alpha", _AXIS_CASES, ids=str)
+def test_axis_assignment_against_kronecker_sums(n, alpha):
+    """One oracle step equals the dense step built from the Kronecker sums of
+    eqs. (2DA)/(3DA)/(newlinear), and the oracle energy equals
+    h^d((1/4)(u^2-1)^T(u^2-1) - (1/2) u^T A u) with that A (Example 5)."""
+    e_two, e_one, e_en = _axis_assignment_errors(n, alpha)
+    assert e_two <= 1e-14 and e_one <= 1e-14 and e_en <= 1e-13, (e_two, e_one, e_en)
+
+
+def _stencil_2d(n, alpha, eps, a, b, u):
+    """The right-hand side of eq. (disFAC) in 2D without the nonlinear term,
+    written with the double indices of the paper: u[j, i] is u_{i,j}, i along
+    x^(1) with (alpha_1, h_1, m_1), j along x^(2) with (alpha_2, h_2, m_2)."""
+    (n1, n2), (a1, a2) = n, alpha
+    m1, m2 = n1 + 1, n2 + 1
+    h1, h2 = (b - a) / m1, (b - a) / m2
+    full = np.zeros((m2 + 1, m1 + 1))
+    full[1:m2, 1:m1] = u
+    w1, w2 = O.omega_weights(a1, m1 + 2), O.omega_weights(a2, m2 + 2)
+    p1 = -eps ** 2 / (2 * h1 ** a1 * math.cos(a1 * math.pi / 2))
+    p2 = -eps ** 2 / (2 * h2 ** a2 * math.cos(a2 * math.pi / 2))
+    out = np.zeros_like(u)
+    for j in range(1, m2):
+        for i in range(1, m1):
+            s1 = sum(w1[k] * full[j, i - k + 1] for k in range(i + 2)) + \
+                sum(w1[k] * full[j, i + k - 1] for k in range(m1 - i + 2))
+            s2 = sum(w2[k] * full[j - k + 1, i] for k in range(j + 2)) + \
+                sum(w2[k] * full[j + k - 1, i] for k in range(m2 - j + 2))
+            out[j - 1, i - 1] = p1 * s1 + p2 * s2
+    return out
+
+
+@pytest.mark.parametrize("n,alpha", [((2, 3), (1.2, 1.8)), ((5, 3), (1.7, 1.3)), ((4, 4), (1.1, 1.9))], ids=str)
+def test_kronecker_sum_is_the_2d_stencil(n, alpha):
+    """The Kronecker sum used by the pins above equals the literal double-index
+    stencil of eq. (disFAC) (alpha_1, h_1 on the index i of x^(1)), so the pins
+    do not rest on the ordering convention alone."""
+    eps, a, b = 0.3, -1.0, 1.5
+    Bs, _, _ = _axis_pieces(n, alpha, eps, a, b)
+    A = _kron_sum(Bs)
+    u = np.random.default_rng(11).uniform(-1.0, 1.0, tuple(reversed(n)))
+    np.testing.assert_allclose((A @ u.ravel()).reshape(u.shape), _stencil_2d(n, alpha, eps, a, b, u),
+                               rtol=1e-12, atol=1e-12)
+
+
 # ------------------------------------------------------------- energy -------
 
 def _ginzburg_landau_energy(u, n, eps, a, b):
@@ -530,3 +656,48 @@ def test_planted_mistakes_fail_energy_pins(mutant):
         got = O.discrete_energy(u, sch)
     ref = _ginzburg_landau_energy(u, n, 0.3, -1.0, 1.0)
     assert abs(got - ref) > 1e-6 * ref
+
+
+class _AlphaReversed(O.Scheme):
+    """Mutant: the alpha list taken in reverse axis order."""
+
+    def __init__(self, n, alpha, *args, **kw):
+        super().__init__(n, tuple(reversed(alpha)), *args, **kw)
+
+
+class _HOfOtherAxis(O.Scheme):
+    """Mutant: each axis's h computed from the mirrored axis's n."""
+
+    def __init__(self, n, alpha, eps, tau, a=-1.0, b=1.0, kind="two_level", route="dense"):
+        super().__init__(n, alpha, eps, tau, a, b, kind, route)
+        build = {"two_level": O.axis_two_level_factor, "one_level": O.axis_one_level_factor,
+                 "adi": O.axis_adi_factor}[kind]
+        mirrored = list(reversed(self.n))
+        self.P = [build(self.alpha[ax], self.eps, (self.b - self.a) / (mirrored[ax] + 1), nn, self.tau)
+                  for ax, nn in enumerate(self.n)]
+
+
+def _mirrored_apply_axis(u, P, axis):
+    """Mutant: paper axis l taken as numpy axis l - 1 (x^(1) slowest)."""
+    ax = axis - 1
+    return np.moveaxis(np.tensordot(P, u, axes=([1], [ax])), 0, ax)
+
+
+@pytest.mark.parametrize("mutant", [("Scheme", _AlphaReversed), ("Scheme", _HOfOtherAxis),
+                                    ("apply_axis", _mirrored_apply_axis)],
+                         ids=["alpha-reversed", "h-of-other-axis", "memory-axis-mirrored"])
+@pytest.mark.parametrize("n,alpha", [_AXIS_CASES[0], _AXIS_CASES[3]], ids=str)
+def test_planted_axis_mixups_fail_kronecker_pins(mutant, n, alpha):
+    with _Mutant(*mutant):
+        e_two, e_one, e_en = _axis_assignment_errors(n, alpha)
+    assert e_two > 1e-6 and e_one > 1e-6, (e_two, e_one, e_en)
+
+
+@pytest.mark.parametrize("mutant", [("Scheme", _AlphaReversed), ("apply_axis", _mirrored_apply_axis)],
+                         ids=["alpha-reversed", "memory-axis-mirrored"])
+def test_planted_axis_mixups_fail_on_a_square_grid(mutant):
+    """On a square grid with distinct alpha per axis only the alpha assignment
+    tells the axes apart; both mix-ups still fail (the energy pin included)."""
+    with _Mutant(*mutant):
+        e_two, e_one, e_en = _axis_assignment_errors(*_AXIS_CASES[1])
+    assert e_two > 1e-6 and e_one > 1e-6 and e_en > 1e-6, (e_two, e_one, e_en)
