@@ -263,7 +263,10 @@ sfac_status sfac_batch_set_wait_limit(sfac_batch* batch, long long spin_limit, i
  * counters first, and calls whose work overlaps on the GPU race, so serialise
  * them. The first call on each device looks up the array's device address
  * (with the batch's device made current); make that first call before any
- * stream capture. Report status with sfac_batch_wait as for sfac_batch_launch. */
+ * stream capture. The address is kept per device and context: after a context
+ * reset (e.g. cudaDeviceReset) the next call on that device looks it up again,
+ * so make that call before any capture too. Report status with sfac_batch_wait
+ * as for sfac_batch_launch. */
 sfac_status sfac_batch_launch_noalloc(sfac_batch* batch, void* stream);
 
 /* ------------------------------------------------------------------------ */
@@ -275,7 +278,10 @@ sfac_status sfac_batch_launch_noalloc(sfac_batch* batch, void* stream);
  * resident in the arena until its result is fetched; twists and twiddles are
  * held once per server for every line length. A round advances every active slot by
  * up to `chunk` steps in one persistent launch of the batched kernel, so
- * requests admitted while a round runs join the next round. A slot always
+ * requests admitted while rounds run join a later round. Up to two rounds may
+ * be in flight: the second is enqueued behind the first (each has its own
+ * schedule, counters and status word), so the caller can collect the first
+ * round's finished requests while the device runs the second. A slot always
  * advances in whole chunks counted from its own first step, so its result does
  * not depend on which other requests share its rounds. */
 typedef struct sfac_server sfac_server;
@@ -301,26 +307,61 @@ sfac_status sfac_server_request_bytes(const sfac_params* params, size_t* bytes);
 sfac_status sfac_server_admit(sfac_server* server, const sfac_params* params, const void* u0_host,
                               long long nsteps, int* slot);
 
-/* Launch one round on `stream`: every slot with steps left advances by
- * min(chunk, steps left) steps (kernel shape `shape`, an index as in
- * sfac_batch_set_config). Asynchronous; at most one round in flight. */
-sfac_status sfac_server_round(sfac_server* server, long long chunk, int shape, void* stream);
+/* Enqueue one round on `stream`: every slot with steps left that no round in
+ * flight already covers advances by min(chunk, those steps) steps (kernel
+ * shape `shape`, an index as in sfac_batch_set_config). Asynchronous: the
+ * schedule goes up through pinned memory, so the call does not wait for a
+ * round in flight; the new round starts on the device after that round ends
+ * (also on another stream). At most two rounds in flight (SFAC_EINVAL
+ * otherwise). *launched (may be NULL) receives 1 if a round was enqueued, 0 if
+ * no slot had open steps (then nothing is enqueued). */
+sfac_status sfac_server_round(sfac_server* server, long long chunk, int shape, void* stream, int* launched);
 
-/* Wait for the round in flight (synchronises `stream`) and list the slots whose
- * steps are all done: up to max_finished slot numbers go to finished[],
- * *nfinished receives their count. SFAC_ETIMEOUT if a dependency wait gave up. */
+/* Wait for the oldest round in flight (host wait on its completion event; a
+ * later round keeps running) and list the slots that have no steps left and
+ * no round in flight: up to max_finished slot numbers go to finished[],
+ * *nfinished receives their count. With no round in flight: SFAC_OK and none.
+ * If a dependency wait of the round gave up, every slot of that round is
+ * marked failed (its field is partly advanced), the call returns SFAC_ETIMEOUT
+ * and still lists the slots that are finished, the failed ones among them once
+ * no round in flight holds them; later rounds skip failed slots. */
 sfac_status sfac_server_wait(sfac_server* server, void* stream, int* finished, int max_finished,
                              int* nfinished);
 
 /* Copy a slot's field to u_host (if not NULL; on the internal copy stream,
- * synchronised, so it may overlap a round in flight that does not include the
- * slot) and, if release != 0, free its slot and arena block. */
+ * synchronised, so it may overlap rounds in flight that do not include the
+ * slot) and, if release != 0, free its slot and arena block. SFAC_EINVAL if a
+ * round in flight still holds the slot. For a failed slot nothing is copied
+ * and the call returns SFAC_ETIMEOUT (after freeing the slot if release != 0). */
 sfac_status sfac_server_fetch(sfac_server* server, int slot, void* u_host, int release);
+
+/* Failure-detection controls of the server's rounds, as sfac_batch_set_wait_limit:
+ * every dependency wait polls at most spin_limit times; hold_slot >= 0 makes
+ * the next round that advances that slot wait on a count that is never reached
+ * in the slot's second pass, so the round gives up (-1: off; the hook acts on
+ * one round only). Host-only. The paper has no counterpart. */
+sfac_status sfac_server_set_wait_limit(sfac_server* server, long long spin_limit, int hold_slot);
 
 /* Free arena bytes, largest free block, slots in use and slot capacity (each
  * pointer may be NULL). */
 sfac_status sfac_server_info(const sfac_server* server, size_t* free_bytes, size_t* largest_free,
                              int* active, int* capacity);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Microbenchmark of the SMs' multiply-add rate: the ALU roofline the FP64 and
+ * FP32 axis passes are reported against. The paper has no counterpart.
+ * Enqueues one kernel of `blocks` CTAs of 256 threads on `stream`; every thread
+ * runs 8 independent chains x <- fma(x, a, b) for 16 * iters rounds and writes
+ * one value to out_dev[thread], which must hold blocks * 256 elements (double
+ * for kind 0, float otherwise). kind 0: FP64 fma; 1: FP32 fmaf; 2: the packed
+ * two-lane FP32 multiply-add (each chain a pair of floats). The launch executes
+ * blocks * 256 * 8 * 16 * iters multiply-adds (kind 2: twice as many lanes),
+ * 2 flops each. Asynchronous: time it with events on `stream`.
+ * SFAC_EINVAL for an unknown kind, blocks < 1, iters < 1 or a NULL buffer. */
+sfac_status sfac_probe_fma(int kind, int blocks, long long iters, void* out_dev, void* stream);
 
 /* Message describing the calling thread's most recent failure ("" if none). */
 const char* sfac_last_error(void);

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
+#include <memory>
 #include <new>
 #include <string>
 #include <thread>
@@ -87,6 +89,12 @@ struct sfac_batch {
 };
 
 namespace {
+struct BatchDeleter {
+    void operator()(sfac_batch* B) const { sfac_batch_destroy(B); }
+};
+}  // namespace
+
+namespace {
 
 sfac_status check_params(const sfac_params& p, int prec0) {
     if (p.dim != 2 && p.dim != 3) return bfail(SFAC_EUNSUPPORTED, "batch instances must be 2D or 3D");
@@ -124,11 +132,9 @@ void set_items(BatchInst& I, int es, int mult) {
     for (int a = I.dim; a < 3; ++a) I.items[a] = 0;
 }
 
-// Build the phase schedule of `inst` (fields and steps already set) and upload
-// it into the device buffer `*dev` (grown as needed), filling `sc` except the
-// scratch pointers.
-sfac_status upload_schedule(const std::vector<BatchInst>& inst, int mult, void** dev, size_t* cap,
-                            BatchSchedule* sc, cudaStream_t st) {
+// Build the phase schedule of `inst` into `blob` (the seven arrays below, each
+// 256-byte aligned) and record its layout.
+void pack_schedule(const std::vector<BatchInst>& inst, std::vector<unsigned char>& blob, ScheduleLayout* lay) {
     const int n_inst = (int)inst.size();
     long long max_steps = 0;
     for (const BatchInst& I : inst) max_steps = std::max<long long>(max_steps, I.steps);
@@ -172,12 +178,16 @@ sfac_status upload_schedule(const std::vector<BatchInst>& inst, int mult, void**
     const size_t sizes[7] = {sz_inst, 8 * phase_base.size(), 8 * phase_first.size(),
                              8 * std::max<size_t>(slot_cum.size(), 1), 4 * std::max<size_t>(phase_step.size(), 1),
                              4 * std::max<size_t>(phase_axis.size(), 1), 4 * std::max<size_t>(slot_inst.size(), 1)};
-    size_t off[7], total = 0;
+    size_t total = 0;
     for (int q = 0; q < 7; ++q) {
-        off[q] = total;
+        lay->off[q] = total;
         total += align256(sizes[q]);
     }
-    std::vector<unsigned char> blob(total, 0);
+    lay->total = total;
+    lay->nphase = (int)phase_step.size();
+    lay->total_items = phase_base.back();
+    blob.assign(total, 0);
+    const size_t* off = lay->off;
     if (n_inst) std::memcpy(blob.data() + off[0], inst.data(), sizeof(BatchInst) * n_inst);
     std::memcpy(blob.data() + off[1], phase_base.data(), 8 * phase_base.size());
     std::memcpy(blob.data() + off[2], phase_first.data(), 8 * phase_first.size());
@@ -185,6 +195,28 @@ sfac_status upload_schedule(const std::vector<BatchInst>& inst, int mult, void**
     if (!phase_step.empty()) std::memcpy(blob.data() + off[4], phase_step.data(), 4 * phase_step.size());
     if (!phase_axis.empty()) std::memcpy(blob.data() + off[5], phase_axis.data(), 4 * phase_axis.size());
     if (!slot_inst.empty()) std::memcpy(blob.data() + off[6], slot_inst.data(), 4 * slot_inst.size());
+}
+
+void bind_schedule(const ScheduleLayout& lay, void* dev, int mult, BatchSchedule* sc) {
+    unsigned char* base = static_cast<unsigned char*>(dev);
+    sc->inst = reinterpret_cast<const BatchInst*>(base + lay.off[0]);
+    sc->phase_base = reinterpret_cast<const long long*>(base + lay.off[1]);
+    sc->phase_first = reinterpret_cast<const long long*>(base + lay.off[2]);
+    sc->slot_cum = reinterpret_cast<const long long*>(base + lay.off[3]);
+    sc->phase_step = reinterpret_cast<const int*>(base + lay.off[4]);
+    sc->phase_axis = reinterpret_cast<const int*>(base + lay.off[5]);
+    sc->slot_inst = reinterpret_cast<const int*>(base + lay.off[6]);
+    sc->nphase = lay.nphase;
+    sc->mult = mult;
+    sc->total_items = lay.total_items;
+}
+
+sfac_status upload_schedule(const std::vector<BatchInst>& inst, int mult, void** dev, size_t* cap,
+                            BatchSchedule* sc, cudaStream_t st) {
+    std::vector<unsigned char> blob;
+    ScheduleLayout lay{};
+    pack_schedule(inst, blob, &lay);
+    const size_t total = lay.total;
     cudaError_t err;
     if (total > *cap) {
         if (*dev) {
@@ -204,17 +236,7 @@ sfac_status upload_schedule(const std::vector<BatchInst>& inst, int mult, void**
     err = cudaMemcpyAsync(*dev, blob.data(), total, cudaMemcpyHostToDevice, st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) return bcuda(err, "schedule upload");
-    unsigned char* base = static_cast<unsigned char*>(*dev);
-    sc->inst = reinterpret_cast<const BatchInst*>(base + off[0]);
-    sc->phase_base = reinterpret_cast<const long long*>(base + off[1]);
-    sc->phase_first = reinterpret_cast<const long long*>(base + off[2]);
-    sc->slot_cum = reinterpret_cast<const long long*>(base + off[3]);
-    sc->phase_step = reinterpret_cast<const int*>(base + off[4]);
-    sc->phase_axis = reinterpret_cast<const int*>(base + off[5]);
-    sc->slot_inst = reinterpret_cast<const int*>(base + off[6]);
-    sc->nphase = (int)phase_step.size();
-    sc->mult = mult;
-    sc->total_items = phase_base.back();
+    bind_schedule(lay, *dev, mult, sc);
     return SFAC_OK;
 }
 
@@ -340,6 +362,36 @@ sfac_status batch_launch_with_scratch(sfac_batch* B, unsigned long long* scratch
     return SFAC_OK;
 }
 
+// Runs fn(w, nth) for every share w in [0, nth): shares 1.. on host threads,
+// share 0 and any share whose thread could not be started on the calling
+// thread. Every started thread is joined before this returns or throws, and an
+// exception thrown by a share is rethrown here (the first one), so no
+// exception escapes a thread and no joinable thread is left behind.
+template <class F>
+void run_shares(unsigned nth, F fn) {
+    std::vector<std::exception_ptr> errs(nth);
+    auto share = [&](unsigned w) {
+        try {
+            fn(w, nth);
+        } catch (...) {
+            errs[w] = std::current_exception();
+        }
+    };
+    std::vector<std::thread> pool;
+    unsigned started = 1;
+    try {
+        pool.reserve(nth);
+        for (; started < nth; ++started) pool.emplace_back(share, started);
+    } catch (...) {
+        // thread creation failed: the shares not started run below
+    }
+    share(0);
+    for (unsigned w = started; w < nth; ++w) share(w);
+    for (auto& t : pool) t.join();
+    for (const auto& e : errs)
+        if (e) std::rethrow_exception(e);
+}
+
 int batch_count(const sfac_batch* B) { return B->count; }
 int batch_device(const sfac_batch* B) { return B->device; }
 
@@ -355,7 +407,10 @@ sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream
         const sfac_status st = check_params(params[i], params[0].prec);
         if (st != SFAC_OK) return bfail(st, "instance " + std::to_string(i) + ": " + sfac_last_error());
     }
-    sfac_batch* B = new (std::nothrow) sfac_batch();
+    // Owned here until it is handed out: every early return or exception below
+    // releases what was allocated so far.
+    std::unique_ptr<sfac_batch, BatchDeleter> owner(new (std::nothrow) sfac_batch());
+    sfac_batch* B = owner.get();
     if (!B) return bfail(SFAC_ENOMEM, "host allocation failed");
     B->count = count;
     B->prec = params[0].prec;
@@ -364,20 +419,13 @@ sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream
     cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, B->device);
     // FP64 precompute of every instance's axes, spread over host threads.
     std::vector<sfac::AxisHost> host((size_t)count * 3);
-    {
-        unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-        std::vector<std::thread> pool;
-        for (unsigned w = 0; w < nth; ++w) {
-            pool.emplace_back([&, w]() {
-                for (int i = (int)w; i < count; i += (int)nth) {
-                    const sfac_params& p = params[i];
-                    for (int a = 0; a < p.dim; ++a)
-                        sfac::compute_axis(p.alpha[a], p.eps, p.tau, p.a, p.b, p.n[a], &host[(size_t)i * 3 + a]);
-                }
-            });
+    sfac::run_shares(std::max(1u, std::min(16u, std::thread::hardware_concurrency())), [&](unsigned w, unsigned nth) {
+        for (int i = (int)w; i < count; i += (int)nth) {
+            const sfac_params& p = params[i];
+            for (int a = 0; a < p.dim; ++a)
+                sfac::compute_axis(p.alpha[a], p.eps, p.tau, p.a, p.b, p.n[a], &host[(size_t)i * 3 + a]);
         }
-        for (auto& t : pool) t.join();
-    }
+    });
     const bool f64 = B->prec == SFAC_FP64;
     const size_t rs = f64 ? sizeof(double) : sizeof(float);
     // Per instance and axis the two spectral factors; twists and twiddles depend
@@ -409,10 +457,7 @@ sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream
         }
     {
         const sfac_status cs = sfac::make_common_tables(B->prec, &B->dev_common);
-        if (cs != SFAC_OK) {
-            sfac_batch_destroy(B);
-            return cs;
-        }
+        if (cs != SFAC_OK) return cs;
     }
     cudaError_t err = cudaMalloc(&B->dev_tables, total);
     if (err == cudaSuccess)
@@ -420,17 +465,13 @@ sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void**>(&B->host_error), sizeof(int));
     if (err != cudaSuccess) {
         cudaGetLastError();
-        sfac_batch_destroy(B);
         return bfail(SFAC_ENOMEM, std::string("batch allocation: ") + cudaGetErrorString(err));
     }
     *B->host_error = 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     err = cudaMemcpyAsync(B->dev_tables, blob.data(), total, cudaMemcpyHostToDevice, st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
-    if (err != cudaSuccess) {
-        sfac_batch_destroy(B);
-        return bcuda(err, "batch table upload");
-    }
+    if (err != cudaSuccess) return bcuda(err, "batch table upload");
     B->inst.resize(count);
     unsigned char* base = static_cast<unsigned char*>(B->dev_tables);
     for (int i = 0; i < count; ++i) {
@@ -451,7 +492,7 @@ sfac_status sfac_batch_create(const sfac_params* params, int count, void* stream
     }
     B->fields.assign(count, nullptr);
     B->nsteps.assign(count, 0);
-    *out = B;
+    *out = owner.release();
     return SFAC_OK;
 } catch (...) {
     return sfac::abi_exception_status();

@@ -66,6 +66,20 @@ __host__ __device__ constexpr int batch_elems(int N) {
     return N >= 512 ? 16 : ES;
 }
 
+// FP32: the twiddle rows of TwRows<N, batch_elems<ES>(N)> for every length
+// N = 32 .. 512, one after another in shared memory behind the common tables;
+// complex values before those of length N, and in all.
+template <int ES>
+__host__ __device__ constexpr int batch_rows_offset(int N) {
+    int off = 0;
+    for (int M = 32; M < N; M *= 2) off += tw_rows_elems(M, batch_elems<ES>(M), M);
+    return off;
+}
+template <int ES>
+__host__ __device__ constexpr int batch_rows_elems() {
+    return batch_rows_offset<ES>(1024);
+}
+
 // One warp-group of lines (32/T lines, see warp_pass_lines) of either axis
 // kind; kept out of line so that each (R, N, E) body is compiled once per
 // kernel and shared by both axis kinds.
@@ -79,7 +93,7 @@ __device__ __noinline__ void batch_lines(const PassArgs& pa, bool strided, long 
     const Ex ex{region + j * Ex::LINE_ELEMS};
     C2<R> x[E];
     line.template load<E>(x, t);
-    fused_pass<R, N, E, false>(x, t, pa, ex);
+    fused_pass<R, N, E, false, false, (sizeof(R) == 4)>(x, t, pa, ex);
     line.template store<E>(x, t);
 }
 
@@ -97,15 +111,21 @@ __device__ __noinline__ void batch_lines_staged(const PassArgs& pa, C2<R>* stage
     C2<R> x[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) x[e] = line[t + e * T];
-    fused_pass<R, N, E, false>(x, t, pa, ex);
+    fused_pass<R, N, E, false, false, (sizeof(R) == 4)>(x, t, pa, ex);
 #pragma unroll
     for (int e = 0; e < E; ++e) line[t + e * T] = x[e];
 }
 
+// Complex values of the twiddle rows of one launch (FP32 only).
+template <typename R, int ES>
+__host__ __device__ constexpr int batch_rows_of() {
+    return sizeof(R) == 4 ? batch_rows_elems<ES>() : 0;
+}
+
 // Bytes of dynamic shared memory of one launch.
-template <typename R>
+template <typename R, int ES>
 __host__ __device__ constexpr size_t batch_smem_bytes(int wpb, int stage) {
-    return sizeof(C2<R>) * ((size_t)wpb * BATCH_REGION + BATCH_COMMON_ELEMS +
+    return sizeof(C2<R>) * ((size_t)wpb * BATCH_REGION + BATCH_COMMON_ELEMS + batch_rows_of<R, ES>() +
                             (stage > 0 ? (size_t)wpb * batch_stage_elems(stage) : 0));
 }
 
@@ -123,9 +143,20 @@ batch_kernel(const BatchSchedule b) {
     C2<R>* common = reinterpret_cast<C2<R>*>(smem_raw) + (blockDim.x >> 5) * BATCH_REGION;
     const C2<R>* gcommon = static_cast<const C2<R>*>(b.common);
     for (int i = threadIdx.x; i < BATCH_COMMON_ELEMS; i += blockDim.x) common[i] = gcommon[i];
+    // FP32: the twiddle rows of every length, from the global twiddle tables.
+    C2<R>* rows = common + BATCH_COMMON_ELEMS;
+    if constexpr (sizeof(R) == 4) {
+        C2<float>* r = reinterpret_cast<C2<float>*>(rows);
+        const C2<float>* g = reinterpret_cast<const C2<float>*>(gcommon);
+        build_tw_rows<32, batch_elems<ES>(32)>(r + batch_rows_offset<ES>(32), g + batch_common_offset(32), threadIdx.x, blockDim.x);
+        build_tw_rows<64, batch_elems<ES>(64)>(r + batch_rows_offset<ES>(64), g + batch_common_offset(64), threadIdx.x, blockDim.x);
+        build_tw_rows<128, batch_elems<ES>(128)>(r + batch_rows_offset<ES>(128), g + batch_common_offset(128), threadIdx.x, blockDim.x);
+        build_tw_rows<256, batch_elems<ES>(256)>(r + batch_rows_offset<ES>(256), g + batch_common_offset(256), threadIdx.x, blockDim.x);
+        build_tw_rows<512, 16>(r + batch_rows_offset<ES>(512), g + batch_common_offset(512), threadIdx.x, blockDim.x);
+    }
     __syncthreads();
     // This warp's staging buffer for strided items (b.stage > 0, FP32).
-    C2<R>* stage = common + BATCH_COMMON_ELEMS + (b.stage > 0 ? warp * batch_stage_elems(b.stage) : 0);
+    C2<R>* stage = rows + batch_rows_of<R, ES>() + (b.stage > 0 ? warp * batch_stage_elems(b.stage) : 0);
     int p = 0;  // phase of the last item: claimed items increase, so p only moves forward
     for (;;) {
         unsigned long long item = 0;
@@ -177,6 +208,7 @@ batch_kernel(const BatchSchedule b) {
         pa.eC = I.tab[a][0];
         pa.eS = I.tab[a][1];
         pa.twid = common + batch_common_offset(N);
+        pa.twrows = rows + batch_rows_offset<ES>(N);
         pa.twist = common + batch_common_offset(N) + N;
         // J^Q_{tau/2} opens step 0 and closes the last step; inner steps merge
         // the closing and opening halves into J^Q_tau.
@@ -277,7 +309,7 @@ template <typename R, int ES>
 cudaError_t setup_batch(int wpb, int stage, int sms, int* grid) {
     if (wpb < 1 || wpb > 8 || stage < 0 || stage > 4) return cudaErrorInvalidValue;
     auto kern = wpb <= 4 ? batch_kernel<R, ES, 128, batch_small_minb<R>()> : batch_kernel<R, ES, 256, 1>;
-    const size_t smem = batch_smem_bytes<R>(wpb, stage);
+    const size_t smem = batch_smem_bytes<R, ES>(wpb, stage);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
@@ -291,7 +323,7 @@ cudaError_t setup_batch(int wpb, int stage, int sms, int* grid) {
 template <typename R, int ES>
 cudaError_t launch_batch(int wpb, int grid, const BatchSchedule& sc, cudaStream_t s) {
     if (wpb < 1 || wpb > 8 || grid < 1) return cudaErrorInvalidValue;
-    const size_t smem = batch_smem_bytes<R>(wpb, sc.stage);
+    const size_t smem = batch_smem_bytes<R, ES>(wpb, sc.stage);
     if (wpb <= 4)
         batch_kernel<R, ES, 128, batch_small_minb<R>()><<<grid, wpb * 32, smem, s>>>(sc);
     else

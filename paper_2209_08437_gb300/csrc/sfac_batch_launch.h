@@ -76,6 +76,24 @@ cudaError_t launch_batch_f64(int wpb, int es, int grid, const BatchSchedule& sc,
 // thread below N = 512 and `mult` warp-groups per item.
 void set_items(BatchInst& I, int es, int mult);
 
+// Byte offsets of the seven arrays of a packed schedule (instances,
+// phase_base, phase_first, slot_cum, phase_step, phase_axis, slot_inst), its
+// size and counts.
+struct ScheduleLayout {
+    size_t off[7];
+    size_t total;
+    int nphase;
+    long long total_items;
+};
+
+// Build the phase schedule of `inst` (fields, steps and items set) into `blob`
+// (host memory, resized to lay->total bytes).
+void pack_schedule(const std::vector<BatchInst>& inst, std::vector<unsigned char>& blob, ScheduleLayout* lay);
+// Point the schedule arrays of `sc` into a device copy of a packed blob at `dev`
+// (its scratch pointers, spin limit, hold instance, common tables and staging
+// are left as they are).
+void bind_schedule(const ScheduleLayout& lay, void* dev, int mult, BatchSchedule* sc);
+
 // Build the phase schedule of `inst` (fields, steps and items set) and upload
 // it into *dev (grown as needed, *cap bytes); fills `sc` except its scratch
 // pointers, spin limit and hold instance. Synchronises `st`.

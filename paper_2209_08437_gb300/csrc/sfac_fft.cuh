@@ -159,19 +159,88 @@ struct Dft<R, 1, INV> {
     static __device__ __forceinline__ void run(C2<R>*) {}
 };
 
-// One Stockham pass (span P) and, recursively, the ones after it.
-// tw[m] = e^{-2 pi i m / N}, m in [0, N).
+// Twiddle sources of the Stockham passes. get<P, RAD>(q, t, k, w) fills w[r],
+// r in [1, RAD), with e^{-2 pi i r k / (P RAD)} for butterfly k = (t + q T)
+// mod P of the pass of span P (w[0] is left as it is).
+//
+// TwTable reads them from the length-N table tw[m] = e^{-2 pi i m / N}.
+template <typename R, int N>
+struct TwTable {
+    const C2<R>* __restrict__ tw;
+    template <int P, int RAD>
+    __device__ __forceinline__ void get(int, int, int k, C2<R> (&w)[RAD]) const {
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) w[r] = tw[r * k * (N / (P * RAD))];
+    }
+};
+
+// TwRows (FP32) reads them from rows laid out per pass and thread: for every
+// pass of span P > 1, for q in [0, Q) and t in [0, T), one row holding the RAD
+// factors of butterfly (t + q T) mod P (entry 0 is 1), padded to
+// tw_row_stride(RAD) values. A thread loads its row with 16-byte loads (two
+// factors each), and the rows of the 8 lanes of a quarter-warp start in
+// distinct 16-byte bank groups, so the loads are free of bank conflicts; the
+// table-indexed loads of TwTable hit the same bank for r k multiples of 16 and
+// were the largest share of shared-memory traffic of the FP32 passes. The
+// values are the table's, so results are bit-identical to TwTable's.
+__host__ __device__ constexpr int tw_row_stride(int rad) { return rad == 2 ? 2 : rad + 2; }
+
+// Radix of the pass of span P for a line of N points with E values per thread.
+__host__ __device__ constexpr int fft_pass_radix(int N, int E, int P) { return (P * E <= N) ? E : (N / P); }
+
+// Complex values of the rows of every pass of span < P_END (P_END = N: all).
+__host__ __device__ constexpr int tw_rows_elems(int N, int E, int P_END) {
+    int total = 0;
+    for (int P = fft_pass_radix(N, E, 1); P < N && P < P_END; P *= fft_pass_radix(N, E, P)) {
+        const int rad = fft_pass_radix(N, E, P);
+        total += (E / rad) * (N / E) * tw_row_stride(rad);
+    }
+    return total;
+}
+
+template <int N, int E>
+struct TwRows {
+    const C2<float>* __restrict__ rows;
+    template <int P, int RAD>
+    __device__ __forceinline__ void get(int q, int t, int, C2<float> (&w)[RAD]) const {
+        constexpr int T = N / E, S = tw_row_stride(RAD);
+        const float4* row = reinterpret_cast<const float4*>(rows + tw_rows_elems(N, E, P) + (q * T + t) * S);
+#pragma unroll
+        for (int h = 0; h < RAD / 2; ++h) {
+            const float4 v = row[h];
+            if (h > 0) w[2 * h] = {v.x, v.y};
+            w[2 * h + 1] = {v.z, v.w};
+        }
+    }
+};
+
+// Fill the rows of TwRows<N, E> from the table tw (threads tid of nth share the work).
+template <int N, int E>
+__device__ __forceinline__ void build_tw_rows(C2<float>* rows, const C2<float>* tw, int tid, int nth) {
+    constexpr int T = N / E;
+    for (int P = fft_pass_radix(N, E, 1); P < N; P *= fft_pass_radix(N, E, P)) {
+        const int rad = fft_pass_radix(N, E, P), S = tw_row_stride(rad), Q = E / rad;
+        C2<float>* base = rows + tw_rows_elems(N, E, P);
+        for (int f = tid; f < Q * T * S; f += nth) {
+            const int q = f / (T * S), t = (f / S) % T, r = f % S;
+            const int k = (t + q * T) & (P - 1);
+            base[f] = r < rad ? tw[r * k * (N / (P * rad))] : C2<float>{0.f, 0.f};
+        }
+    }
+}
+
+// One Stockham pass (span P) and, recursively, the ones after it; twiddles
+// from `tws` (TwTable or TwRows).
 template <typename R, int N, int E, int P, bool INV>
 struct FftPass {
-    static constexpr int RAD = (P * E <= N) ? E : (N / P);
+    static constexpr int RAD = fft_pass_radix(N, E, P);
     static constexpr bool LAST = (P * RAD == N);
     static constexpr int T = N / E;
     static constexpr int Q = E / RAD;
     static_assert(RAD >= 2 && (RAD & (RAD - 1)) == 0 && RAD <= 32, "radix");
 
-    template <class Ex>
-    static __device__ __forceinline__ void run(C2<R> (&x)[E], int t, const C2<R>* __restrict__ tw,
-                                               const Ex& ex) {
+    template <class Ex, class Tw>
+    static __device__ __forceinline__ void run(C2<R> (&x)[E], int t, const Tw& tws, const Ex& ex) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int i = t + q * T;
@@ -180,11 +249,10 @@ struct FftPass {
 #pragma unroll
             for (int r = 0; r < RAD; ++r) a[r] = x[q + r * Q];
             if constexpr (P > 1) {
+                C2<R> w[RAD];
+                tws.template get<P, RAD>(q, t, k, w);
 #pragma unroll
-                for (int r = 1; r < RAD; ++r) {
-                    const C2<R> w = tw[r * k * (N / (P * RAD))];
-                    a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
-                }
+                for (int r = 1; r < RAD; ++r) a[r] = INV ? cmulc(a[r], w[r]) : cmul(a[r], w[r]);
             }
             Dft<R, RAD, INV>::run(a);
             if constexpr (LAST) {
@@ -201,16 +269,23 @@ struct FftPass {
 #pragma unroll
             for (int e = 0; e < E; ++e) x[e] = ex.get(t + e * T);
             Ex::sync();
-            FftPass<R, N, E, P * RAD, INV>::run(x, t, tw, ex);
+            FftPass<R, N, E, P * RAD, INV>::run(x, t, tws, ex);
         }
     }
 };
 
-// Unnormalised FFT of one line held as described above (INV: inverse, no 1/N).
+// Unnormalised FFT of one line held as described above (INV: inverse, no 1/N),
+// twiddles from the table tw[m] = e^{-2 pi i m / N}.
 template <typename R, int N, int E, bool INV, class Ex>
 __device__ __forceinline__ void line_fft(C2<R> (&x)[E], int t, const C2<R>* __restrict__ tw,
                                          const Ex& ex) {
-    FftPass<R, N, E, 1, INV>::run(x, t, tw, ex);
+    FftPass<R, N, E, 1, INV>::run(x, t, TwTable<R, N>{tw}, ex);
+}
+
+// The same with the twiddles from a source object (TwTable or TwRows).
+template <typename R, int N, int E, bool INV, class Ex, class Tw>
+__device__ __forceinline__ void line_fft_tw(C2<R> (&x)[E], int t, const Tw& tws, const Ex& ex) {
+    FftPass<R, N, E, 1, INV>::run(x, t, tws, ex);
 }
 
 // ---------------------------------------------------------------------------

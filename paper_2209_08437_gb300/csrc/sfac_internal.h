@@ -48,6 +48,9 @@ struct PassArgs {
     const void* twist;
     const void* twid;
     const void* rtwid = nullptr;
+    // FP32 warp-local passes: the per-thread twiddle rows of TwRows<N, E>
+    // (sfac_fft.cuh), built in shared memory by the kernel (NULL otherwise).
+    const void* twrows = nullptr;
     double jq_in_E, jq_in_1mE;
     double jq_out_E, jq_out_1mE;
     int jq_in, jq_out;
@@ -65,7 +68,7 @@ constexpr unsigned int SFAC_PASS_TIMEOUT = 1u;
 
 // Values per thread of the FP64 CTA pass for FFT length N. Lengths up to 1024
 // (E <= 8) run their FFTs with ratio twiddles.
-constexpr int f64_elems_per_thread(int N) { return N >= 2048 ? 16 : (N < 8 ? N : 8); }
+__host__ __device__ constexpr int f64_elems_per_thread(int N) { return N >= 2048 ? 16 : (N < 8 ? N : 8); }
 
 // Launch one pass for line length N (a power of two in [4, 4096]).
 // Returns cudaErrorInvalidValue for an unsupported N.

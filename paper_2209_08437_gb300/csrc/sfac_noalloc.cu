@@ -20,9 +20,14 @@
 //    serialised by the caller;
 //  - the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
-//    before capturing any stream;
+//    before capturing any stream. The address is kept per device together
+//    with the device's current context: after a context reset (for example
+//    cudaDeviceReset) the array lives in a new context, so the next call finds
+//    a different context and looks the address up again (again before any
+//    capture);
 //  - the batch must already be prepared (sfac_batch_prepare), which is where
 //    its tables and schedule were allocated.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -41,6 +46,8 @@ static __device__ __align__(256) unsigned long long g_noalloc_scratch[kMaxInstan
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Per device: the context the address was looked up in, and the address.
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 unsigned long long* g_scratch_addr[kMaxDevices] = {};
 
 sfac_status nfail(sfac_status st, const std::string& msg) {
@@ -48,17 +55,45 @@ sfac_status nfail(sfac_status st, const std::string& msg) {
     return st;
 }
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
+// cuCtxGetCurrent, looked up through the runtime (no link against the driver
+// library); NULL if the driver does not provide it.
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+CtxGetCurrent ctx_get_current() {
+    static const CtxGetCurrent fn = []() -> CtxGetCurrent {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<CtxGetCurrent>(p);
+    }();
+    return fn;
+}
+
+// The calling thread's current context (NULL if none or unknown).
+CUcontext current_context() {
+    CUcontext c = nullptr;
+    const CtxGetCurrent fn = ctx_get_current();
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
+
+// Device address of g_noalloc_scratch on the current device: looked up once
+// per device and context (set-up), with that device current.
 sfac_status scratch_address(int dev, unsigned long long** out) {
     if (dev < 0 || dev >= kMaxDevices) return nfail(SFAC_EUNSUPPORTED, "device index too large");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    const CUcontext ctx = current_context();
+    if (!g_scratch_addr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
         void* ptr = nullptr;
         const cudaError_t err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (err != cudaSuccess)
             return nfail(SFAC_ECUDA, std::string("cudaGetSymbolAddress of the static scratch: ") +
                                          cudaGetErrorString(err));
         g_scratch_addr[dev] = static_cast<unsigned long long*>(ptr);
+        g_scratch_ctx[dev] = current_context();  // the lookup made the device's context current
     }
     *out = g_scratch_addr[dev];
     return SFAC_OK;

@@ -97,6 +97,32 @@ __device__ __forceinline__ void apply_spectral(C2<R> (&x)[E], int t, const C2<R>
     line_fft<R, N, E, true>(x, t, tw, ex);
 }
 
+// The same with the twiddles from a source object (TwTable or TwRows).
+template <typename R, int N, int E, class Ex, class Tw>
+__device__ __forceinline__ void apply_spectral_tw(C2<R> (&x)[E], int t, const Tw& tws, const Ex& ex,
+                                                  const R* __restrict__ m) {
+    constexpr int T = N / E;
+    line_fft_tw<R, N, E, false>(x, t, tws, ex);
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = cscale(x[e], m[t + e * T]);
+    line_fft_tw<R, N, E, true>(x, t, tws, ex);
+}
+
+// Twiddle source of the FP32 passes: the per-thread rows a.twrows (ROWS) or
+// the table a.twid.
+template <typename R, int N, int E, bool ROWS>
+struct TwOf {
+    static __device__ __forceinline__ TwTable<R, N> make(const PassArgs& a) {
+        return TwTable<R, N>{static_cast<const C2<R>*>(a.twid)};
+    }
+};
+template <int N, int E>
+struct TwOf<float, N, E, true> {
+    static __device__ __forceinline__ TwRows<N, E> make(const PassArgs& a) {
+        return TwRows<N, E>{static_cast<const C2<float>*>(a.twrows)};
+    }
+};
+
 // The same with the FFTs on ratio twiddles (FP64, E <= 8; table rt).
 template <int N, int E, class Ex>
 __device__ __forceinline__ void apply_spectral_ratio(C2<double> (&x)[E], int t, const double* __restrict__ rt,
@@ -173,11 +199,11 @@ __device__ __forceinline__ void two_level_chain(C2<R> (&x)[E], int t, const Pass
 
 // d += the increments of e^{tau/2 C}, e^{tau S}, e^{tau/2 C} in turn (each
 // applied to x0 + d), rolled as described above.
-template <typename R, int N, int E, bool PADDED, class Ex, class X0>
+template <typename R, int N, int E, bool PADDED, bool ROWS, class Ex, class X0>
 __device__ __forceinline__ void three_factors_rolled(const X0& x0, C2<R> (&d)[E], int t, const PassArgs& a,
                                                      const Ex& ex) {
     constexpr int T = N / E;
-    const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
+    const auto tws = TwOf<R, N, E, ROWS>::make(a);
     const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
     C2<R> y[E];
 #pragma unroll 1
@@ -191,7 +217,7 @@ __device__ __forceinline__ void three_factors_rolled(const X0& x0, C2<R> (&d)[E]
         }
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
-            line_fft<R, N, E, false>(y, t, tw, ex);
+            line_fft_tw<R, N, E, false>(y, t, tws, ex);
             if (h == 0) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
@@ -225,7 +251,7 @@ __device__ __forceinline__ void three_factors_rolled(const X0& x0, C2<R> (&d)[E]
 //
 // X0 gives x0 element by element (x0.get(e) = element t + e T, see RegX0).
 // On return d holds the total increment.
-template <typename R, int N, int E, bool PADDED, class Ex, class X0>
+template <typename R, int N, int E, bool PADDED, bool ROWS, class Ex, class X0>
 __device__ __forceinline__ void two_level_increment(const X0& x0, C2<R> (&d)[E], int t, const PassArgs& a,
                                                     const Ex& ex) {
     if (a.jq_in) {
@@ -240,10 +266,10 @@ __device__ __forceinline__ void two_level_increment(const X0& x0, C2<R> (&d)[E],
         for (int e = 0; e < E; ++e) d[e] = {R(0), R(0)};
     }
     if constexpr (N <= SFAC_ROLLED_MAX_N) {
-        three_factors_rolled<R, N, E, PADDED>(x0, d, t, a, ex);
+        three_factors_rolled<R, N, E, PADDED, ROWS>(x0, d, t, a, ex);
     } else {
         constexpr int T = N / E;
-        const C2<R>* __restrict__ tw = static_cast<const C2<R>*>(a.twid);
+        const auto tw = TwOf<R, N, E, ROWS>::make(a);
         const C2<R>* __restrict__ twist = static_cast<const C2<R>*>(a.twist);
         const R* __restrict__ eC = static_cast<const R*>(a.eC);
         const R* __restrict__ eS = static_cast<const R*>(a.eS);
@@ -251,7 +277,7 @@ __device__ __forceinline__ void two_level_increment(const X0& x0, C2<R> (&d)[E],
         // e^{tau/2 C}
 #pragma unroll
         for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
-        apply_spectral<R, N, E>(y, t, tw, ex, eC);
+        apply_spectral_tw<R, N, E>(y, t, tw, ex, eC);
         if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
         for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
@@ -259,21 +285,21 @@ __device__ __forceinline__ void two_level_increment(const X0& x0, C2<R> (&d)[E],
         if constexpr (PADDED) {
 #pragma unroll
             for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
-            apply_spectral<R, N, E>(y, t, tw, ex, eS);
+            apply_spectral_tw<R, N, E>(y, t, tw, ex, eS);
             zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
             for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
         } else {
 #pragma unroll
             for (int e = 0; e < E; ++e) y[e] = cmul(cadd(x0.get(e), d[e]), ldg_c2(twist + t + e * T));
-            apply_spectral<R, N, E>(y, t, tw, ex, eS);
+            apply_spectral_tw<R, N, E>(y, t, tw, ex, eS);
 #pragma unroll
             for (int e = 0; e < E; ++e) d[e] = cadd(d[e], cmulc(y[e], ldg_c2(twist + t + e * T)));
         }
         // e^{tau/2 C}
 #pragma unroll
         for (int e = 0; e < E; ++e) y[e] = cadd(x0.get(e), d[e]);
-        apply_spectral<R, N, E>(y, t, tw, ex, eC);
+        apply_spectral_tw<R, N, E>(y, t, tw, ex, eC);
         if constexpr (PADDED) zero_tail<R, N, E>(y, t, a.nmem);
 #pragma unroll
         for (int e = 0; e < E; ++e) d[e] = cadd(d[e], y[e]);
@@ -295,20 +321,22 @@ struct RegX0 {
     __device__ __forceinline__ C2<R> get(int e) const { return x[e]; }
 };
 
-template <typename R, int N, int E, bool PADDED, class Ex>
+template <typename R, int N, int E, bool PADDED, bool ROWS, class Ex>
 __device__ __forceinline__ void two_level_pass_incr(C2<R> (&x0)[E], int t, const PassArgs& a, const Ex& ex) {
     C2<R> d[E];
-    two_level_increment<R, N, E, PADDED>(RegX0<R, E>{x0}, d, t, a, ex);
+    two_level_increment<R, N, E, PADDED, ROWS>(RegX0<R, E>{x0}, d, t, a, ex);
 #pragma unroll
     for (int e = 0; e < E; ++e) x0[e] = cadd(x0[e], d[e]);
 }
 
 // One whole pass on the line held in x: FP32 in increment form, FP64 plain
-// (RATIO: FFTs on the ratio twiddles of a.rtwid).
-template <typename R, int N, int E, bool PADDED, bool RATIO = false, class Ex>
+// (RATIO: FFTs on the ratio twiddles of a.rtwid; ROWS, FP32: twiddles from
+// the per-thread rows a.twrows).
+template <typename R, int N, int E, bool PADDED, bool RATIO = false, bool ROWS = false, class Ex>
 __device__ __forceinline__ void fused_pass(C2<R> (&x)[E], int t, const PassArgs& a, const Ex& ex) {
+    static_assert(!ROWS || sizeof(R) == 4, "twiddle rows: FP32 passes");
     if constexpr (sizeof(R) == 4) {
-        two_level_pass_incr<R, N, E, PADDED>(x, t, a, ex);
+        two_level_pass_incr<R, N, E, PADDED, ROWS>(x, t, a, ex);
     } else {
         if (a.jq_in) jq_all<R, E>(x, a.jq_in_E, a.jq_in_1mE);
         two_level_chain<R, N, E, PADDED, RATIO>(x, t, a, ex);
@@ -545,7 +573,8 @@ axis_pass_kernel(const PassArgs a) {
 
     C2<R> x[E];
     line.template load<E>(x, t);
-    fused_pass<R, N, E, PADDED, (sizeof(R) == 8 && E <= 8)>(x, t, a, ex);
+    // ratio-twiddle records exist for the FP64 pass's default values per thread only
+    fused_pass<R, N, E, PADDED, (sizeof(R) == 8 && E <= 8 && E == f64_elems_per_thread(N))>(x, t, a, ex);
     line.template store<E>(x, t);
 }
 
@@ -557,14 +586,17 @@ axis_pass_kernel(const PassArgs a) {
 // a + a/E. With lanes laid out as (line, t), the first-pass writes (at t*E + r)
 // and the reads (at t + e*T) of every pass hit distinct banks in each
 // half-warp, also when a half-warp holds several short lines.
-template <typename R, int N, int E>
+// LE: distance of the lines' regions (default N + N/E).
+template <typename R, int N, int E, int LE = N + N / E>
 struct WarpExchange {
-    static constexpr int SH = E == 32 ? 5 : (E == 16 ? 4 : 3);
+    // (E = 2, 4: one pad per 16 values)
+    static constexpr int SH = E == 32 ? 5 : (E == 16 ? 4 : (E == 8 ? 3 : 4));
     C2<R>* base;
     __device__ __forceinline__ void put(int idx, C2<R> v) const { base[idx + (idx >> SH)] = v; }
     __device__ __forceinline__ C2<R> get(int idx) const { return base[idx + (idx >> SH)]; }
     static __device__ __forceinline__ void sync() { __syncwarp(); }
-    static constexpr int LINE_ELEMS = N + N / E;
+    static constexpr int LINE_ELEMS = LE;
+    static_assert(LE >= N + N / E, "line region too small");
 };
 
 // Lines [first, first + 32/T) of the pass `a`, processed by one warp. `region`
@@ -579,15 +611,20 @@ __device__ __forceinline__ void warp_pass_lines(const PassArgs& a, long long fir
     const Ex ex{region + j * Ex::LINE_ELEMS};
     C2<R> x[E];
     line.template load<E, CG>(x, t);
-    fused_pass<R, N, E, PADDED>(x, t, a, ex);
+    fused_pass<R, N, E, PADDED, false, (sizeof(R) == 4)>(x, t, a, ex);
     line.template store<E>(x, t);
 }
 
 // Shared-memory tables of one axis for the persistent kernels: eC[N], eS[N],
-// twist[N] (not for padded passes) and twiddles[N], copied once per CTA.
-template <typename R, int N, bool PADDED>
+// twist[N] (not for padded passes), twiddles[N] and, for FP32 passes with E
+// values per thread, the twiddle rows of TwRows<N, E>; copied (built) once per
+// CTA. The rows start 16-byte aligned (the dynamic shared memory is).
+template <typename R, int N, int E, bool PADDED>
 struct SmemTables {
-    static constexpr size_t BYTES = 2 * N * sizeof(R) + (PADDED ? 1 : 2) * N * sizeof(C2<R>);
+    static constexpr bool ROWS = sizeof(R) == 4;
+    static constexpr size_t HEAD = 2 * N * sizeof(R) + (PADDED ? 1 : 2) * N * sizeof(C2<R>);
+    static constexpr size_t ROWS_OFF = (HEAD + 15) / 16 * 16;
+    static constexpr size_t BYTES = ROWS ? ROWS_OFF + sizeof(C2<R>) * (size_t)tw_rows_elems(N, E, N) : HEAD;
     static __device__ __forceinline__ void load(PassArgs& a, unsigned char* smem) {
         R* eC = reinterpret_cast<R*>(smem);
         R* eS = eC + N;
@@ -602,6 +639,11 @@ struct SmemTables {
             eS[i] = gS[i];
             tw[i] = gtw[i];
             if (!PADDED) twist[i] = gtwist[i];
+        }
+        if constexpr (ROWS) {
+            C2<float>* rows = reinterpret_cast<C2<float>*>(smem + ROWS_OFF);
+            build_tw_rows<N, E>(rows, reinterpret_cast<const C2<float>*>(gtw), threadIdx.x, blockDim.x);
+            a.twrows = rows;
         }
         __syncthreads();
         a.eC = eC;
@@ -619,9 +661,9 @@ axis_pass_warp_kernel(const PassArgs a0, long long ngroups) {
     constexpr int LPW = 32 / (N / E);  // lines per warp
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PassArgs a = a0;
-    SmemTables<R, N, PADDED>::load(a, smem_raw);
+    SmemTables<R, N, E, PADDED>::load(a, smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C2<R>* region = reinterpret_cast<C2<R>*>(smem_raw + SmemTables<R, N, PADDED>::BYTES) +
+    C2<R>* region = reinterpret_cast<C2<R>*>(smem_raw + SmemTables<R, N, E, PADDED>::BYTES) +
                     warp * LPW * WarpExchange<R, N, E>::LINE_ELEMS;
     for (long long g = (long long)blockIdx.x * WPB + warp; g < ngroups; g += (long long)gridDim.x * WPB) {
         warp_pass_lines<R, N, E, STRIDED, false, PADDED>(a, g * LPW, region, lane);
@@ -700,7 +742,7 @@ cudaError_t launch_cfg(const PassArgs& a, cudaStream_t s) {
 template <typename R, int N, int E, int WPB, bool STRIDED, bool PADDED>
 cudaError_t launch_warp(const PassArgs& a, cudaStream_t s) {
     constexpr int LPW = 32 / (N / E);
-    const size_t smem = SmemTables<R, N, PADDED>::BYTES +
+    const size_t smem = SmemTables<R, N, E, PADDED>::BYTES +
                         sizeof(C2<R>) * (size_t)WPB * LPW * WarpExchange<R, N, E>::LINE_ELEMS;
     auto kern = axis_pass_warp_kernel<R, N, E, WPB, STRIDED, PADDED>;
     static LaunchSetup setup;
@@ -716,17 +758,57 @@ cudaError_t launch_warp(const PassArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// SMs of the current device (cached per device; 0 if unknown).
+inline int current_device_sms() {
+    static std::atomic<int> cache[LaunchSetup::kMaxDevices] = {};
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= LaunchSetup::kMaxDevices) {
+        cudaGetLastError();
+        return 0;
+    }
+    if ((sms = cache[dev].load()) != 0) return sms;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cache[dev].store(sms);
+    return sms;
+}
+
+// Values per thread that give a line 32 threads (at least 2 values): the
+// shape of the small-grid passes below.
+template <int N>
+constexpr int warp_line_elems() {
+    return N / 32 >= 2 ? N / 32 : 2;
+}
+
 template <typename R, int N, bool PADDED>
 cudaError_t launch_n(const PassArgs& a, cudaStream_t s) {
     constexpr int E = elems_per_thread<N>();
     constexpr int T = N / E;
     // the host builds the FP64 ratio-twiddle records for this E
     static_assert(sizeof(R) != 8 || E == f64_elems_per_thread(N), "FP64 values per thread");
+    // Small grids: when the default shape would leave SMs without work, each
+    // line gets a warp of its own (N/32 values per thread, one line per CTA or
+    // warp), so that as many SMs as there are lines work on it. The passes are
+    // then latency bound; a shorter per-thread chain and more SMs beat fewer,
+    // fuller threads. Same arithmetic, other exchange schedule.
+    constexpr int ES = warp_line_elems<N>();
+    const int sms = current_device_sms();
     if constexpr (sizeof(R) == 4 && N >= 32 && N <= 512) {
         // FP32: warp-local lines with 16 values per thread. Two warps per CTA
         // for long lines (few lines: many small CTAs spread better over 152
         // SMs), four otherwise.
         constexpr int WPB = N >= 512 ? 2 : 4;
+        constexpr int LPW = 32 / (N / 16);
+        // (not below N = 128: on the 64^2 grid one CTA of four 8-line warps was
+        // faster than 32 one-line warps, 1.01 against 1.14 ms per 100 steps)
+        if constexpr (ES < 16 && N >= 128) {
+            if ((a.clines + LPW - 1) / LPW < sms) {
+                if (a.inner > 1) return launch_warp<R, N, ES, 1, true, PADDED>(a, s);
+                return launch_warp<R, N, ES, 1, false, PADDED>(a, s);
+            }
+        }
         if (a.inner > 1) return launch_warp<R, N, 16, WPB, true, PADDED>(a, s);
         return launch_warp<R, N, 16, WPB, false, PADDED>(a, s);
     } else if constexpr (sizeof(R) == 4 && N >= 1024) {
@@ -748,6 +830,16 @@ cudaError_t launch_n(const PassArgs& a, cudaStream_t s) {
         constexpr int MIN_S = (T >= 256 || sizeof(R) == 8) ? 1 : 32 / (2 * (int)sizeof(R));
         constexpr int LPC_S = (TPB / T) > MIN_S ? (TPB / T) : MIN_S;
         constexpr int LPC_C = (TPB / T) > 1 ? (TPB / T) : 1;
+        if constexpr (sizeof(R) == 8 && N >= 32 && N <= 256) {
+            // FP64 small grids: fewer CTAs than the SMs' two CTA slots -> one
+            // line per 32-thread CTA (E = N/32; complex twiddles unless E is
+            // the default, whose ratio records the plan holds)
+            const int lpc = a.inner > 1 ? LPC_S : LPC_C;
+            if ((a.clines + lpc - 1) / lpc < 2LL * sms) {
+                if (a.inner > 1) return launch_cfg<R, N, ES, 1, true, PADDED>(a, s);
+                return launch_cfg<R, N, ES, 1, false, PADDED>(a, s);
+            }
+        }
         if (a.inner > 1) return launch_cfg<R, N, E, LPC_S, true, PADDED>(a, s);
         return launch_cfg<R, N, E, LPC_C, false, PADDED>(a, s);
     }

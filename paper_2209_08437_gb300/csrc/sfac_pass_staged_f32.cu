@@ -50,8 +50,20 @@ struct StagedShape {
     // four warps (168 registers a thread at N = 256, no spills; their shared
     // memory fits three times too); one 8-warp CTA at N = 512.
     static constexpr int MINB = WPB <= 4 ? 3 : 1;
-    static constexpr int XCH_ELEMS = WPB * LPW * WarpExchange<float, N, E>::LINE_ELEMS;
-    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + SmemTables<float, N, false>::BYTES +
+    // Lane layout. Default: lane = j T + t (line j, thread t of the line).
+    // With 64-byte tile rows and two lines per warp (N = 256) each half-warp
+    // would read 16 consecutive rows of one line, and under the 64-byte
+    // swizzle those rows cover only 8 of the 16 eight-byte bank slots (a 2-way
+    // conflict on every tile read and write). There the lanes interleave the
+    // lines instead, lane = t LPW + j: a half-warp reads 8 rows of both lines,
+    // which fill all 16 slots. The exchange regions of the two lines are then
+    // 8 values apart modulo 16 (LE = N + N/E + 8), so that the exchanges stay
+    // free of conflicts too.
+    static constexpr bool INTERLEAVE = (BW == 16 && LPW == 2);
+    static constexpr int LE = N + N / E + (INTERLEAVE ? 8 : 0);
+    using Ex = WarpExchange<float, N, E, LE>;
+    static constexpr int XCH_ELEMS = WPB * LPW * LE;
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + SmemTables<float, N, E, false>::BYTES +
                                    sizeof(C2<float>) * XCH_ELEMS + 8 * (STAGES + 1);
     static_assert(BW == 32 || BW == 16, "tile rows are 64 or 128 bytes");
     static_assert(STAGE_BYTES % 1024 == 0, "stage buffers keep the swizzle atom alignment");
@@ -92,11 +104,11 @@ axis_pass_staged_kernel(const __grid_constant__ CUtensorMap tmap, const PassArgs
                         long long ntiles) {
     using Sh = StagedShape<N>;
     constexpr int E = Sh::E, T = Sh::T, LPW = Sh::LPW, BW = Sh::BW, S = Sh::STAGES;
-    using Ex = WarpExchange<float, N, E>;
+    using Ex = typename Sh::Ex;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* stage0 = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* tabs = stage0 + S * Sh::STAGE_BYTES;
-    C2<float>* xch = reinterpret_cast<C2<float>*>(tabs + SmemTables<float, N, false>::BYTES);
+    C2<float>* xch = reinterpret_cast<C2<float>*>(tabs + SmemTables<float, N, E, false>::BYTES);
     uint64_t* full = reinterpret_cast<uint64_t*>(xch + Sh::XCH_ELEMS);
     uint64_t* never = full + S;  // no arrival ever completes it (the hold test hook)
 
@@ -108,7 +120,7 @@ axis_pass_staged_kernel(const __grid_constant__ CUtensorMap tmap, const PassArgs
         fence_mbar_init();
     }
     PassArgs a = a0;
-    SmemTables<float, N, false>::load(a, tabs);  // ends with __syncthreads
+    SmemTables<float, N, E, false>::load(a, tabs);  // ends with __syncthreads
 
     const long long first = blockIdx.x, step = gridDim.x;
     const long long mine = first < ntiles ? (ntiles - 1 - first) / step + 1 : 0;
@@ -132,7 +144,8 @@ axis_pass_staged_kernel(const __grid_constant__ CUtensorMap tmap, const PassArgs
     if (leader)
         for (; issued < S - 1 && issued < mine; ++issued) issue(issued);
 
-    const int j = lane / T, t = lane % T;
+    const int j = Sh::INTERLEAVE ? lane % LPW : lane / T;
+    const int t = Sh::INTERLEAVE ? lane / LPW : lane % T;
     const Ex ex{xch + (warp * LPW + j) * Ex::LINE_ELEMS};
     long long k = 0;
     bool failed = false;
@@ -149,7 +162,7 @@ axis_pass_staged_kernel(const __grid_constant__ CUtensorMap tmap, const PassArgs
 #pragma unroll
             for (int e = 0; e < E; ++e) x[e] = {0.f, 0.f};
         }
-        fused_pass<float, N, E, false>(x, t, a, ex);
+        fused_pass<float, N, E, false, false, true>(x, t, a, ex);
         if (ok) line.store(x, t);
         fence_proxy_async_smem();
         if (__syncthreads_or(!ok)) {

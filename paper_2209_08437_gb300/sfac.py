@@ -81,11 +81,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sfac_server_destroy": (ctypes.c_int, [vp]),
         "sfac_server_request_bytes": (ctypes.c_int, [P(SfacParams), P(ctypes.c_size_t)]),
         "sfac_server_admit": (ctypes.c_int, [vp, P(SfacParams), vp, ll, P(ctypes.c_int)]),
-        "sfac_server_round": (ctypes.c_int, [vp, ll, ctypes.c_int, vp]),
+        "sfac_server_round": (ctypes.c_int, [vp, ll, ctypes.c_int, vp, P(ctypes.c_int)]),
+        "sfac_server_set_wait_limit": (ctypes.c_int, [vp, ll, ctypes.c_int]),
         "sfac_server_wait": (ctypes.c_int, [vp, vp, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]),
         "sfac_server_fetch": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
         "sfac_server_info": (ctypes.c_int, [vp, P(ctypes.c_size_t), P(ctypes.c_size_t), P(ctypes.c_int),
                                             P(ctypes.c_int)]),
+        "sfac_probe_fma": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ll, vp, vp]),
         "sfac_last_error": (ctypes.c_char_p, []),
         "sfac_version": (ctypes.c_int, []),
     }
@@ -217,6 +219,17 @@ def sfac_plan_tables(params: SfacParams, axis: int):
     return lam, mu, bcol, jq
 
 
+PROBE_THREADS, PROBE_CHAINS, PROBE_UNROLL = 256, 8, 16
+
+
+def sfac_probe_fma(kind: int, blocks: int, iters: int, out_dev, stream=None) -> float:
+    """Enqueue the multiply-add rate probe; returns the flops the launch performs."""
+    _check(load().sfac_probe_fma(int(kind), int(blocks), int(iters), _ptr(out_dev), _stream(stream)),
+           "sfac_probe_fma")
+    lanes = 2 if kind == 2 else 1
+    return 2.0 * lanes * blocks * PROBE_THREADS * PROBE_CHAINS * PROBE_UNROLL * iters
+
+
 def sfac_last_error() -> str:
     return load().sfac_last_error().decode(errors="replace")
 
@@ -327,15 +340,31 @@ def sfac_server_admit(server: int, params: SfacParams, u0_host, nsteps: int):
     return slot.value
 
 
-def sfac_server_round(server: int, chunk: int, shape: int = 0, stream=None) -> None:
-    _check(load().sfac_server_round(server, int(chunk), int(shape), _stream(stream)), "sfac_server_round")
+def sfac_server_round(server: int, chunk: int, shape: int = 0, stream=None) -> bool:
+    """Enqueue a round; False when no slot had open steps (nothing enqueued)."""
+    launched = ctypes.c_int(0)
+    _check(load().sfac_server_round(server, int(chunk), int(shape), _stream(stream), ctypes.byref(launched)),
+           "sfac_server_round")
+    return bool(launched.value)
 
 
 def sfac_server_wait(server: int, capacity: int, stream=None):
+    """Finished slots of the oldest round in flight. If that round gave up
+    (SFAC_ETIMEOUT), raises SfacError whose `finished` lists the finished
+    slots, failed ones included (fetching those raises SFAC_ETIMEOUT)."""
     buf = (ctypes.c_int * max(capacity, 1))()
     n = ctypes.c_int(0)
-    _check(load().sfac_server_wait(server, _stream(stream), buf, capacity, ctypes.byref(n)), "sfac_server_wait")
-    return [buf[i] for i in range(min(n.value, capacity))]
+    st = load().sfac_server_wait(server, _stream(stream), buf, capacity, ctypes.byref(n))
+    done = [buf[i] for i in range(min(n.value, capacity))]
+    if st != SFAC_OK:
+        err = SfacError(st, "sfac_server_wait", load().sfac_last_error().decode(errors="replace"))
+        err.finished = done
+        raise err
+    return done
+
+
+def sfac_server_set_wait_limit(server: int, spin_limit: int, hold_slot: int = -1) -> None:
+    _check(load().sfac_server_set_wait_limit(server, int(spin_limit), int(hold_slot)), "sfac_server_set_wait_limit")
 
 
 def sfac_server_fetch(server: int, slot: int, u_host=None, release: bool = True) -> None:
@@ -363,8 +392,11 @@ class Server:
         p = make_params(problem.n, problem.alpha, problem.eps, problem.tau, problem.a, problem.b, self.prec)
         return sfac_server_admit(self.handle, p, u0_host, nsteps)
 
-    def round(self, chunk: int, shape: int = 0, stream=None):
-        sfac_server_round(self.handle, chunk, shape, stream)
+    def round(self, chunk: int, shape: int = 0, stream=None) -> bool:
+        return sfac_server_round(self.handle, chunk, shape, stream)
+
+    def set_wait_limit(self, spin_limit: int, hold_slot: int = -1):
+        sfac_server_set_wait_limit(self.handle, spin_limit, hold_slot)
 
     def wait(self, stream=None):
         return sfac_server_wait(self.handle, self.capacity, stream)

@@ -5,8 +5,12 @@
 //    packed two-lane FP32 forms, emulated lane by lane by the host shim);
 //  - ratio twiddles (FP64, E <= 8) with the table of ratio_twiddles; the table
 //    is followed by poison values, so a record read past its end shows up as
-//    a wrong result.
-// Prints one line per case: "<kind> N E INV err" (max error / max |exact|).
+//    a wrong result;
+//  - FP32 with the per-thread twiddle rows of TwRows (built by build_tw_rows
+//    and followed by poison values), which must give bit for bit the results
+//    of the table-indexed twiddles.
+// Prints one line per case: "<kind> N E INV err" (max error / max |exact|),
+// and for the rows "rows32same N E INV 1" when they equal the table results.
 #include <barrier>
 #include <complex>
 #include <cstdio>
@@ -31,9 +35,10 @@ struct HostEx {
 template <typename R>
 std::barrier<>* HostEx<R>::bar = nullptr;
 
-template <typename R, int N, int E, bool INV, bool RATIO>
+template <typename R, int N, int E, bool INV, bool RATIO, bool ROWS = false>
 std::vector<std::complex<double>> run_line(const std::vector<std::complex<double>>& in,
-                                           const std::vector<C2<R>>& tw, const std::vector<double>& rt) {
+                                           const std::vector<C2<R>>& tw, const std::vector<double>& rt,
+                                           const std::vector<C2<R>>* rows = nullptr) {
     constexpr int T = N / E;
     std::vector<C2<R>> buf(N);
     std::barrier<> bar(T);
@@ -46,6 +51,7 @@ std::vector<std::complex<double>> run_line(const std::vector<std::complex<double
             for (int e = 0; e < E; ++e) x[e] = {R(in[t + e * T].real()), R(in[t + e * T].imag())};
             HostEx<R> ex{&buf};
             if constexpr (RATIO) line_fft_ratio<N, E, INV>(x, t, rt.data(), ex);
+            else if constexpr (ROWS) line_fft_tw<R, N, E, INV>(x, t, TwRows<N, E>{rows->data()}, ex);
             else line_fft<R, N, E, INV>(x, t, tw.data(), ex);
             for (int e = 0; e < E; ++e) out[t + e * T] = {double(x[e].x), double(x[e].y)};
         });
@@ -105,10 +111,20 @@ void check(bool ratio) {
         }
         return;
     }
-    const double ef = rel_err<N, false>(in, run_line<R, N, E, false, false>(in, tw, rt));
-    const double ei = rel_err<N, true>(in, run_line<R, N, E, true, false>(in, tw, rt));
+    const auto of = run_line<R, N, E, false, false>(in, tw, rt);
+    const auto oi = run_line<R, N, E, true, false>(in, tw, rt);
+    const double ef = rel_err<N, false>(in, of);
+    const double ei = rel_err<N, true>(in, oi);
     const char* kind = std::is_same<R, double>::value ? "complex64b" : "complex32b";
     printf("%s %d %d 0 %.3e\n%s %d %d 1 %.3e\n", kind, N, E, ef, kind, N, E, ei);
+    if constexpr (std::is_same<R, float>::value) {
+        const int nrows = tw_rows_elems(N, E, N);
+        std::vector<C2<float>> rows(nrows + 64, C2<float>{1e30f, -1e30f});
+        build_tw_rows<N, E>(rows.data(), tw.data(), 0, 1);
+        const auto rf = run_line<R, N, E, false, false, true>(in, tw, rt, &rows);
+        const auto ri = run_line<R, N, E, true, false, true>(in, tw, rt, &rows);
+        printf("rows32same %d %d 0 %d\nrows32same %d %d 1 %d\n", N, E, int(rf == of), N, E, int(ri == oi));
+    }
 }
 
 template <int N>
@@ -117,6 +133,10 @@ void check_all() {
     check<double, N, E64>(false);
     if constexpr (E64 <= 8) check<double, N, E64>(true);
     if constexpr (N >= 32) check<float, N, 16>(false);
+    // the other FP32 shapes: 8 values (batch kernel), N / 32 values (small grids)
+    if constexpr (N >= 16 && N <= 512) check<float, N, 8>(false);
+    if constexpr (N >= 8 && N <= 128) check<float, N, 4>(false);
+    if constexpr (N >= 4 && N <= 64) check<float, N, 2>(false);
 }
 
 int main() {

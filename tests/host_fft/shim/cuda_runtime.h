@@ -8,6 +8,7 @@
 #define __forceinline__ inline
 struct double2 { double x, y; };
 struct float2 { float x, y; };
+struct float4 { float x, y, z, w; };
 inline float2 make_float2(float a, float b) { return {a, b}; }
 // The packed two-lane FP32 operations: each lane rounds as the scalar operation.
 inline float2 __fadd2_rn(float2 a, float2 b) { return {a.x + b.x, a.y + b.y}; }

@@ -74,6 +74,22 @@ def test_null_arguments(lib):
     assert lib.sfac_plan_tables(ctypes.byref(p), 0, None, None, None, None) == S.sfac.SFAC_EINVAL
 
 
+def test_host_checks_of_the_newer_entry_points(lib):
+    """Argument errors of the probe, the server's wait-limit hook and the
+    server round are caught on the host, before any CUDA call."""
+    vp = ctypes.c_void_p
+    assert lib.sfac_probe_fma(3, 1, 1, vp(16), None) == S.sfac.SFAC_EINVAL
+    assert lib.sfac_probe_fma(0, 0, 1, vp(16), None) == S.sfac.SFAC_EINVAL
+    assert lib.sfac_probe_fma(1, 1, 0, vp(16), None) == S.sfac.SFAC_EINVAL
+    assert lib.sfac_probe_fma(2, 1, 1, None, None) == S.sfac.SFAC_EINVAL
+    assert lib.sfac_server_set_wait_limit(None, 10, -1) == S.sfac.SFAC_EINVAL
+    launched = ctypes.c_int(7)
+    assert lib.sfac_server_round(None, 4, 0, None, ctypes.byref(launched)) == S.sfac.SFAC_EINVAL
+    assert launched.value == 0
+    n = ctypes.c_int(5)
+    assert lib.sfac_server_wait(None, None, None, 0, ctypes.byref(n)) == S.sfac.SFAC_EINVAL
+
+
 @pytest.mark.parametrize("n,alpha,eps,tau", [(8, 1.3, 0.1, 0.01), (64, 1.7, 0.05, 1e-3),
                                              (63, 1.5, 0.1, 0.02), (256, 1.2, 0.08, 2e-3),
                                              (1024, 1.3, 0.05, 1e-3)])

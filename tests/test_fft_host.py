@@ -56,8 +56,20 @@ def test_every_length_and_direction_is_covered(results):
                 assert ("complex32b", n, inv) in kinds
 
 
+def test_twiddle_rows_equal_the_table_bit_for_bit(results):
+    """The FP32 passes read their twiddles from per-thread rows (TwRows); the
+    rows hold the table's values, so every line equals the table-indexed FFT
+    exactly, for every FP32 shape (16, 8, 4 and 2 values per thread)."""
+    same = [(n, e, inv, v) for k, n, e, inv, v in results if k == "rows32same"]
+    shapes = {(n, e) for n, e, _, _ in same}
+    assert {(256, 16), (512, 16), (128, 8), (64, 2), (32, 16)} <= shapes
+    assert all(v == 1 for *_, v in same), [s for s in same if s[3] != 1]
+
+
 def test_errors_within_the_rounding_bound(results):
     for kind, n, e, inv, err in results:
+        if kind == "rows32same":
+            continue
         u = 2.0 ** -24 if kind == "complex32b" else 2.0 ** -53
         bound = 4 * max(1, math.log2(n)) * u
         print(f"{kind:10s} N={n:5d} E={e:2d} inv={inv} err={err:.2e} bound={bound:.1e}")

@@ -6,7 +6,9 @@ could synchronise the device, fixed memory budgets). For them the library keeps
 the persistent batch kernel's counters in one fixed device array instead of
 memory the batch allocated. These tests check, through the C ABI, that two such
 launches in a row give the same fields as two launches of the regular entry
-point, and that a batch larger than the array's limit is refused.
+point (bit for bit: both run the same kernel on the same schedule), that they
+leave the device's free memory unchanged, and that a batch larger than the
+array's limit is refused.
 
 Collected last on purpose (file name), so that a run stopping at the first
 failure has already run every other test.
@@ -48,16 +50,21 @@ def test_noalloc_launch_matches_regular_launch_twice(prec):
             b.wait()
         b.prepare(noalloc, steps)
         stream = torch.cuda.current_stream().cuda_stream
+        assert lib.sfac_batch_launch_noalloc(b.handle, stream) == S.sfac.SFAC_OK  # set-up call
+        b.wait()
+        for k, u in enumerate(u0):
+            noalloc[k].copy_(torch.tensor(u, dtype=dt))
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         for _ in range(2):                      # two calls in a row through the C ABI
             assert lib.sfac_batch_launch_noalloc(b.handle, stream) == S.sfac.SFAC_OK
             b.wait()
-    torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free_before   # nothing was allocated
     for k in range(len(probs)):
-        a = regular[k].double().cpu().numpy()
-        c = noalloc[k].double().cpu().numpy()
-        scale = max(1.0, float(np.abs(a).max()))
-        tol = 1e-12 if prec == S.SFAC_FP64 else 1e-6
-        assert np.abs(a - c).max() <= tol * scale, k
+        a = regular[k].cpu().numpy()
+        c = noalloc[k].cpu().numpy()
+        assert np.array_equal(a, c), k
 
 
 def test_noalloc_refuses_batches_above_its_limit():
