@@ -107,12 +107,28 @@ sfac_status sfac_plan_info(const sfac_plan* plan, int axis, int* fft_len, int* p
  * arithmetic. Host-only; nothing is enqueued. */
 sfac_status sfac_plan_kernel(const sfac_plan* plan, int axis, const void* u_dev, int* kind);
 
+/* How sfac_step runs a call of nsteps steps (sfac_plan_step_kernel). The paper
+ * has no counterpart. */
+#define SFAC_STEP_PASSES 0 /* one launch per axis pass */
+#define SFAC_STEP_WHOLE 1  /* small grids: the whole call in one cooperative launch */
+
+/* *kind receives SFAC_STEP_WHOLE if sfac_step(plan, u, nsteps) runs the whole
+ * call in one cooperative launch: two steps or more, every axis a spectral
+ * (not zero-padded) pass of 32..256 points, at most 65536 unknowns, and every
+ * line's warp resident at once on the device (one 32-thread CTA per line pair,
+ * N/32 values per thread). The CTAs meet at a grid-wide barrier between passes;
+ * each wait on it is bounded by the plan's wait limit (sfac_plan_set_wait_limit,
+ * whose hold hook makes the first wait of every CTA run out), and a wait that
+ * runs out is reported by sfac_plan_check. Otherwise SFAC_STEP_PASSES: one
+ * launch per axis pass. Host-only. */
+sfac_status sfac_plan_step_kernel(const sfac_plan* plan, long long nsteps, int* kind);
+
 /* Synchronise `stream`, then report whether an axis pass of this plan gave up
  * on one of its bounded waits since the last check: SFAC_ETIMEOUT if so (the
  * field written by that pass is not valid; the flag is cleared), SFAC_OK
- * otherwise. Only the staged kernel waits (on its tile copies, about two
- * seconds at most per wait); sfac_step_host checks automatically. The paper has
- * no counterpart. */
+ * otherwise. The staged kernel waits on its tile copies and the whole-call
+ * launch of small grids on its grid barrier (about two seconds at most per
+ * wait); sfac_step_host checks automatically. The paper has no counterpart. */
 sfac_status sfac_plan_check(sfac_plan* plan, void* stream);
 
 /* Limit of each bounded wait of the plan's passes, in SM clock cycles

@@ -20,9 +20,9 @@ LIB = os.path.join(LIBDIR, "libsfac.so")
 SOURCES = ["sfac_plan.cu", "sfac_host.cu", "sfac_pass_f64.cu", "sfac_pass_f32.cu", "sfac_pass_pad_f64.cu",
            "sfac_pass_pad_f32.cu", "sfac_batch.cu",
            "sfac_batch_f32.cu", "sfac_batch_f64.cu", "sfac_server.cu",
-           "sfac_noalloc.cu", "sfac_diag.cu", "sfac_pass_staged_f32.cu", "sfac_probe.cu"]
+           "sfac_noalloc.cu", "sfac_diag.cu", "sfac_pass_staged_f32.cu", "sfac_probe.cu", "sfac_steps.cu"]
 HEADERS = ["sfac_fft.cuh", "sfac_pass.cuh", "sfac_internal.h", "sfac_host.h", "sfac_batch.cuh",
-           "sfac_batch_launch.h", "sfac_diag.h", "sfac_tma.cuh"]
+           "sfac_batch_launch.h", "sfac_diag.h", "sfac_tma.cuh", "sfac_steps.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

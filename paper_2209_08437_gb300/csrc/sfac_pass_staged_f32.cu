@@ -8,7 +8,8 @@
 // with one TMA box copy per 256 rows: every row of the tile is BW * 4 = 64 or
 // 128 contiguous bytes, and no thread issues the copy but one. The tile lands
 // in shared memory with the 128-byte (64-byte) swizzle, under which the reads
-// of each warp's lines are free of bank conflicts; the fused pass
+// of each warp's lines are free of bank conflicts at N = 128 and, with the
+// lanes interleaved (StagedShape::INTERLEAVE), at N = 256; the fused pass
 // (sfac_pass.cuh) runs on them unchanged, the results go back into the same
 // tile and one TMA store writes it out.
 //

@@ -15,6 +15,7 @@
 #include "sfac_diag.h"
 #include "sfac_host.h"
 #include "sfac_internal.h"
+#include "sfac_steps.h"
 
 using sfac::AxisHost;
 using sfac::compute_axis;
@@ -109,6 +110,7 @@ struct sfac_plan {
     double3* diag_partial = nullptr;
     double* diag_out = nullptr;
     unsigned int* status = nullptr;       // SFAC_PASS_TIMEOUT bits set by the passes (device)
+    unsigned int* bar = nullptr;          // grid barrier of the whole-call launch (device, 2 words)
     unsigned int* status_host = nullptr;  // pinned host copy of it
     long long wait_cycles = 4LL << 30;
     int hold = 0;
@@ -134,11 +136,11 @@ struct DeviceGuard {
     }
 };
 
-sfac_status launch_axis(sfac_plan* P, void* u, int ax, int jq_in, int jq_out, cudaStream_t st) {
+// Arguments of one pass along axis `ax` of the field u.
+sfac::PassArgs pass_args(const sfac_plan* P, void* u, int ax, int jq_in, int jq_out) {
     long long inner = 1;
     for (int l = 0; l < ax; ++l) inner *= P->p.n[l];
     const int n = P->p.n[ax];
-    const int N = P->ax[ax].fft_len;
     sfac::PassArgs a;
     a.u = u;
     a.inner = inner;
@@ -159,6 +161,12 @@ sfac_status launch_axis(sfac_plan* P, void* u, int ax, int jq_in, int jq_out, cu
     a.status = P->status;
     a.wait_cycles = P->wait_cycles;
     a.hold = P->hold;
+    return a;
+}
+
+sfac_status launch_axis(sfac_plan* P, void* u, int ax, int jq_in, int jq_out, cudaStream_t st) {
+    const sfac::PassArgs a = pass_args(P, u, ax, jq_in, jq_out);
+    const int N = P->ax[ax].fft_len;
     cudaError_t err;
     if (P->ax[ax].padded) {
         err = (P->p.prec == SFAC_FP64) ? sfac::launch_pass_padded_f64(N, a, st) : sfac::launch_pass_padded_f32(N, a, st);
@@ -172,8 +180,50 @@ sfac_status launch_axis(sfac_plan* P, void* u, int ax, int jq_in, int jq_out, cu
     return SFAC_OK;
 }
 
+// Small grids run a whole call of two or more steps in one cooperative launch
+// (sfac_steps.cu): every axis a spectral pass of 32..256 points, at most 65536
+// unknowns, and a grid that is resident at once on the device.
+constexpr long long kStepsMaxPoints = 1LL << 16;
+
+bool steps_shape(const sfac_plan* P) {
+    if (P->npts > kStepsMaxPoints) return false;
+    for (int ax = 0; ax < P->p.dim; ++ax) {
+        const int N = P->ax[ax].fft_len;
+        if (P->ax[ax].padded || N < 32 || N > 256) return false;
+    }
+    return true;
+}
+
+sfac::StepsArgs steps_args(const sfac_plan* P, void* u, long long nsteps) {
+    sfac::StepsArgs g{};
+    for (int ax = 0; ax < P->p.dim; ++ax) {
+        g.ax[ax] = pass_args(P, u, ax, 0, 0);
+        g.n[ax] = P->ax[ax].fft_len;
+    }
+    g.dim = P->p.dim;
+    g.nsteps = nsteps;
+    g.jq_half_E = P->jq_half_E;
+    g.jq_half_1mE = P->jq_half_1mE;
+    g.jq_full_E = P->jq_full_E;
+    g.jq_full_1mE = P->jq_full_1mE;
+    g.bar = P->bar;
+    g.status = P->status;
+    g.wait_cycles = P->wait_cycles;
+    g.hold = P->hold;
+    return g;
+}
+
+bool steps_used(const sfac_plan* P, long long nsteps) {
+    return nsteps >= 2 && steps_shape(P) && sfac::steps_fit(P->p.prec, steps_args(P, nullptr, nsteps));
+}
+
 sfac_status run_steps(sfac_plan* P, void* u, long long nsteps, cudaStream_t st) {
     const int d = P->p.dim;
+    if (steps_used(P, nsteps)) {
+        const cudaError_t err = sfac::launch_steps(P->p.prec, steps_args(P, u, nsteps), st);
+        if (err != cudaSuccess) return cuda_fail(err, "small-grid launch");
+        return SFAC_OK;
+    }
     for (long long s = 0; s < nsteps; ++s) {
         // J^Q_{tau/2} opens the first step and closes the last one; between two
         // steps of one call the closing and opening halves act as one J^Q_{tau}.
@@ -303,6 +353,8 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
     total += align256(4 * sizeof(double));
     const size_t off_status = total;
     total += align256(sizeof(unsigned int));
+    const size_t off_bar = total;
+    total += align256(2 * sizeof(unsigned int));
     std::vector<unsigned char> blob;
     try {
         blob.assign(total, 0);
@@ -382,6 +434,7 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
     P->diag_partial = reinterpret_cast<double3*>(base + off_partial);
     P->diag_out = reinterpret_cast<double*>(base + off_out);
     P->status = reinterpret_cast<unsigned int*>(base + off_status);
+    P->bar = reinterpret_cast<unsigned int*>(base + off_bar);
     err = cudaMallocHost(reinterpret_cast<void**>(&P->status_host), sizeof(unsigned int));
     if (err != cudaSuccess) {
         cudaGetLastError();
@@ -465,6 +518,16 @@ sfac_status sfac_plan_kernel(const sfac_plan* plan, int axis, const void* u_dev,
         *kind = SFAC_KERNEL_WARP;
     else
         *kind = SFAC_KERNEL_CTA;
+    return SFAC_OK;
+} catch (...) {
+    return sfac::abi_exception_status();
+}
+
+sfac_status sfac_plan_step_kernel(const sfac_plan* plan, long long nsteps, int* kind) try {
+    if (!plan || !kind || nsteps < 0) return fail(SFAC_EINVAL, "need a plan, kind and nsteps >= 0");
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(SFAC_ECUDA, "cannot select the plan's device");
+    *kind = steps_used(plan, nsteps) ? SFAC_STEP_WHOLE : SFAC_STEP_PASSES;
     return SFAC_OK;
 } catch (...) {
     return sfac::abi_exception_status();

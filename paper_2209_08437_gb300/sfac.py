@@ -62,6 +62,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sfac_plan_info": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]),
         "sfac_plan_kernel": (ctypes.c_int, [vp, ctypes.c_int, vp, P(ctypes.c_int)]),
         "sfac_plan_check": (ctypes.c_int, [vp, vp]),
+        "sfac_plan_step_kernel": (ctypes.c_int, [vp, ll, P(ctypes.c_int)]),
         "sfac_plan_set_wait_limit": (ctypes.c_int, [vp, ll, ctypes.c_int]),
         "sfac_plan_tables": (ctypes.c_int, [P(SfacParams), ctypes.c_int, P(d), P(d), P(d), P(d)]),
         "sfac_batch_create": (ctypes.c_int, [P(SfacParams), ctypes.c_int, vp, P(vp)]),
@@ -188,6 +189,16 @@ def sfac_plan_kernel(plan: int, axis: int, u) -> int:
     """Which kernel (SFAC_KERNEL_*) a pass along `axis` would run for the field u."""
     kind = ctypes.c_int()
     _check(load().sfac_plan_kernel(plan, int(axis), _ptr(u), ctypes.byref(kind)), "sfac_plan_kernel")
+    return kind.value
+
+
+SFAC_STEP_PASSES, SFAC_STEP_WHOLE = range(2)
+
+
+def sfac_plan_step_kernel(plan: int, nsteps: int) -> int:
+    """SFAC_STEP_WHOLE if sfac_step runs a call of nsteps steps in one launch."""
+    kind = ctypes.c_int()
+    _check(load().sfac_plan_step_kernel(plan, int(nsteps), ctypes.byref(kind)), "sfac_plan_step_kernel")
     return kind.value
 
 
@@ -521,6 +532,10 @@ class Plan:
     def kernel(self, axis: int, u) -> int:
         """SFAC_KERNEL_* that a pass along `axis` runs for the field u."""
         return sfac_plan_kernel(self.handle, axis, u)
+
+    def step_kernel(self, nsteps: int) -> int:
+        """SFAC_STEP_* that sfac_step uses for a call of nsteps steps."""
+        return sfac_plan_step_kernel(self.handle, nsteps)
 
     def check(self, stream=None):
         """Synchronise `stream` and raise if a pass gave up a bounded wait."""
