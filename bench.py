@@ -332,11 +332,13 @@ def measure_small_grid(S, torch, steps, warmup, flush):
             torch.cuda.synchronize()
             graph_ms = timed(graph.replay, max(3, steps // 4))
             del graph
+            whole = plan.step_kernel(nrun) == S.SFAC_STEP_WHOLE
         best = min(statistics.median(run_ms), statistics.median(graph_ms))
         out[name] = {"ms_per_step_single_call": statistics.median(step_ms),
                      "ms_per_run": statistics.median(run_ms), "ms_per_run_graph": statistics.median(graph_ms),
                      "value": problem.points * nrun / (best / 1e3),
-                     "gpu_launches_per_run": nrun * problem.dim}
+                     "whole_call_launch": whole,
+                     "gpu_launches_per_run": 1 if whole else nrun * problem.dim}
     return out
 
 
@@ -376,6 +378,42 @@ def parity_check(S, torch, problem, u0, nsteps):
             got = u.double().cpu().numpy()
         err = float(np.abs(got - ref).max())
         out[key] = err / float(np.abs(ref).max()) if prec == S.SFAC_FP64 else err
+    return out
+
+
+def full_run_parity(S, torch, key, problem, u0):
+    """The whole run of the 3D workload (500 steps, one sfac_step call per
+    path) against the oracle's field stored at 4096 points
+    (tests/golden/config3_oracle_spectral_500.txt, written from oracle/ only),
+    and the FP32 field against the FP64 one everywhere."""
+    if key != "3d256":
+        return None
+    path = os.path.join(ROOT, "tests", "golden", "config3_oracle_spectral_500.txt")
+    if not os.path.exists(path):
+        return None
+    idx, val, max_abs = [], [], None
+    for line in open(path):
+        if line.startswith("# max_abs"):
+            max_abs = float(line.split()[2])
+        elif line.strip() and not line.startswith("#"):
+            i, v = line.split()
+            idx.append(int(i))
+            val.append(float(v))
+    idx, val = np.array(idx), np.array(val)
+    out = {"steps": problem.steps, "reference": "oracle (spectral route) at 4096 stored points"}
+    fields = {}
+    for prec, name in ((S.SFAC_FP64, "f64"), (S.SFAC_FP32, "f32")):
+        dt = torch.float64 if prec == S.SFAC_FP64 else torch.float32
+        with S.Plan.for_problem(problem, prec) as plan:
+            u = torch.tensor(u0, dtype=dt, device="cuda")
+            plan.step(u, problem.steps)
+            plan.check()
+            fields[name] = u.double()
+    f64 = fields["f64"].reshape(-1).cpu().numpy()
+    f32 = fields["f32"].reshape(-1).cpu().numpy()
+    out["f64_rel_err"] = float(np.abs(f64[idx] - val).max()) / max_abs
+    out["f32_max_err"] = float(np.abs(f32[idx] - val).max())
+    out["f32_vs_f64_full_field"] = float((fields["f32"] - fields["f64"]).abs().max())
     return out
 
 
@@ -668,6 +706,8 @@ def main():
         return 0
 
     parity = parity_check(S, torch, problem, u0, parity_steps) if parity_steps > 0 else None
+    if parity is not None and extras:
+        parity["full_run"] = full_run_parity(S, torch, key, problem, u0)
     # the oracle's CPU baseline is timed at N = 1 only
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(problem, u0)
     f64, f32 = head["f64"], head["f32"]
