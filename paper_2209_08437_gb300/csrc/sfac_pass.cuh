@@ -53,14 +53,14 @@ __device__ __forceinline__ R jq_flow(R v, R E, R omE) {
     return v * rsqrt_r(fma(v * v, omE, E));
 }
 
-// Increment of J^Q for the FP32 passes: with q = (1 - E)(1 - v)(1 + v) the
+// Increment of J^Q for the FP32 passes: with q = (1 - E)(1 - v^2) the
 // flow is v / sqrt(1 - q) = v + v q / (s (1 + s)), s = sqrt(1 - q); this returns
 // the added term v q / (s (1 + s)) = v q r / (1 + s) with r = 1/s. The term is
 // about tau |v| at most, so the few-ulp reciprocal square root and fast divide
 // used here change the result by far less than the final rounding of x0 + d.
 // (1 - q >= E > 0, so both are in range.)
 __device__ __forceinline__ float jq_increment(float v, float omE) {
-    const float q = omE * (1.f - v) * (1.f + v);
+    const float q = omE * fmaf(-v, v, 1.f);  // (1 - E)(1 - v^2), 1 - v^2 rounded once
     const float r = rsqrtf(1.f - q);
     const float s = (1.f - q) * r;
     return __fdividef(v * q * r, 1.f + s);
