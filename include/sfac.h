@@ -379,6 +379,19 @@ sfac_status sfac_server_info(const sfac_server* server, size_t* free_bytes, size
  * SFAC_EINVAL for an unknown kind, blocks < 1, iters < 1 or a NULL buffer. */
 sfac_status sfac_probe_fma(int kind, int blocks, long long iters, void* out_dev, void* stream);
 
+/* The nonlinear flow J^Q_s(v) = v / sqrt(E + (1 - E) v^2), E = e^{-2s} (the
+ * exact solution of u' = u - u^3 over time s, Sec. 2.2), evaluated on n values
+ * by the very device code the passes use: v times the double reciprocal
+ * square root of E + (1 - E) v^2 in the FP64 passes, v plus the increment of
+ * the FP32 passes (which use 1 - E only). It lets a test measure that code's error value by value; the paper
+ * has no counterpart. prec SFAC_FP64 / SFAC_FP32 sets the element type of
+ * v_dev and out_dev (n elements each, device memory, may be the same buffer);
+ * E in (0, 1] and one_minus_E = 1 - E as the plans compute them. Enqueued on
+ * `stream`, asynchronous. SFAC_EINVAL for another prec, n < 0 or n > 2^36,
+ * NULL buffers with n > 0, or E outside (0, 1]; n = 0 enqueues nothing. */
+sfac_status sfac_probe_jq(int prec, const void* v_dev, void* out_dev, long long n, double E,
+                          double one_minus_E, void* stream);
+
 /* Message describing the calling thread's most recent failure ("" if none). */
 const char* sfac_last_error(void);
 

@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sfac_server_info": (ctypes.c_int, [vp, P(ctypes.c_size_t), P(ctypes.c_size_t), P(ctypes.c_int),
                                             P(ctypes.c_int)]),
         "sfac_probe_fma": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ll, vp, vp]),
+        "sfac_probe_jq": (ctypes.c_int, [ctypes.c_int, vp, vp, ll, ctypes.c_double, ctypes.c_double, vp]),
         "sfac_last_error": (ctypes.c_char_p, []),
         "sfac_version": (ctypes.c_int, []),
     }
@@ -239,6 +240,12 @@ def sfac_probe_fma(kind: int, blocks: int, iters: int, out_dev, stream=None) -> 
            "sfac_probe_fma")
     lanes = 2 if kind == 2 else 1
     return 2.0 * lanes * blocks * PROBE_THREADS * PROBE_CHAINS * PROBE_UNROLL * iters
+
+
+def sfac_probe_jq(prec: int, v_dev, out_dev, E: float, one_minus_E: float, stream=None) -> None:
+    """Enqueue J^Q on the values of v_dev (the passes' own device code) into out_dev."""
+    _check(load().sfac_probe_jq(int(prec), _ptr(v_dev), _ptr(out_dev), int(v_dev.numel()), float(E),
+                                float(one_minus_E), _stream(stream)), "sfac_probe_jq")
 
 
 def sfac_last_error() -> str:
