@@ -178,12 +178,37 @@ sfac_status sfac_axis_pass(sfac_plan* plan, void* u_dev, int axis, int jq_in, in
  * fixed order (deterministic). u_dev is read only. Synchronises `stream`. */
 sfac_status sfac_diagnostics(sfac_plan* plan, const void* u_dev, double* out, void* stream);
 
-/* End-to-end variant on HOST memory: copy u_host (plan precision, layout above)
- * to a plan-owned device buffer, advance it by nsteps, copy it back into u_host.
- * u_host may be pageable or pinned; pinned memory gives full copy bandwidth.
- * Blocks until the result is in u_host. The staging buffer is allocated on the
- * first call and kept by the plan. Not safe to call concurrently on one plan. */
+/* End-to-end variant on HOST memory: advance u_host (plan precision, layout
+ * above) by nsteps through a plan-owned device buffer and leave the result in
+ * u_host. u_host may be pageable or pinned; the route (sfac_plan_host_route)
+ * is one of
+ *   SFAC_HOST_COPY       cudaMemcpyAsync in, the steps, cudaMemcpyAsync out;
+ *   SFAC_HOST_MAPPED     the first pass of the call loads the field from u_host
+ *                        and the last pass stores the result into it: pinned
+ *                        memory is mapped into the device's address space, so
+ *                        the transfers ride inside those two passes (over
+ *                        NVLink-C2C on GB300) and no copy runs;
+ *   SFAC_HOST_MAPPED_IN  the first pass loads from u_host, a copy brings the
+ *                        result back.
+ * Every route gives the same bits as sfac_step on a device field. Blocks until
+ * the result is in u_host. The staging buffer is allocated on the first call
+ * and kept by the plan. Not safe to call concurrently on one plan. */
 sfac_status sfac_step_host(sfac_plan* plan, void* u_host, long long nsteps, void* stream);
+
+#define SFAC_HOST_COPY 0
+#define SFAC_HOST_MAPPED 1
+#define SFAC_HOST_MAPPED_IN 2
+
+/* *route receives the SFAC_HOST_* route sfac_step_host(plan, u_host, nsteps)
+ * takes. A mapped route needs pinned (page-locked, CUDA-registered) u_host,
+ * 16-byte aligned, nsteps >= 1, the per-pass launches (not the whole-call
+ * launch of small grids) and at least 4096 complex lines (line pairs) in both
+ * the first and the last pass, so that the link's latency hides behind other
+ * lines' work; otherwise SFAC_HOST_COPY. It is SFAC_HOST_MAPPED_IN for an FP32
+ * plan whose last axis has an FFT length above 512 (whose pass would write
+ * rows too narrow for the link). Host-only; nothing is enqueued. The paper has
+ * no counterpart. */
+sfac_status sfac_plan_host_route(const sfac_plan* plan, const void* u_host, long long nsteps, int* route);
 
 /* Host-only: the FP64 tables sfac_plan_create computes for axis `axis` (0-based)
  * of `params`, without touching any GPU. Each output pointer may be NULL; a

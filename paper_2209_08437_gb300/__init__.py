@@ -11,5 +11,6 @@ from .sfac import (SFAC_FP32, SFAC_FP64, Batch, Plan, Server, SfacError, SfacPar
                    sfac_server_create,
                    sfac_server_destroy, sfac_server_request_bytes, sfac_server_admit, sfac_server_round,
                    sfac_server_wait, sfac_server_fetch, sfac_server_info, sfac_server_set_wait_limit,
-                   sfac_probe_fma, sfac_probe_jq, sfac_plan_step_kernel, SFAC_STEP_PASSES, SFAC_STEP_WHOLE)
+                   sfac_probe_fma, sfac_probe_jq, sfac_plan_step_kernel, SFAC_STEP_PASSES, SFAC_STEP_WHOLE,
+                   sfac_plan_host_route, SFAC_HOST_COPY, SFAC_HOST_MAPPED, SFAC_HOST_MAPPED_IN)
 from .serving import serve  # noqa: F401

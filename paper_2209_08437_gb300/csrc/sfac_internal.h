@@ -62,6 +62,12 @@ struct PassArgs {
     // wait for a barrier that nothing completes, so that the limit runs out.
     long long wait_cycles = 4LL << 30;
     int hold = 0;
+    // Store base minus load base, in elements: 0 for a pass in place. A pass
+    // that moves the field between host memory mapped into the device's
+    // address space and device memory loads from u and stores to u + out_shift
+    // (host_io != 0); such passes run on the plain-load kernels, never TMA.
+    long long out_shift = 0;
+    int host_io = 0;
 };
 
 constexpr unsigned int SFAC_PASS_TIMEOUT = 1u;

@@ -357,17 +357,20 @@ __device__ __forceinline__ T ld_field(const T* p) {
 // p0 + idx * stride for a strided pass. PADDED: lines hold nmem < N values
 // (loads beyond them give zeros, stores stop there) and a strided pass with an
 // odd inner extent moves its two columns as scalars (the second may not exist).
+// Stores go out_shift elements past the loads (PassArgs::out_shift).
 template <typename R, int N, bool STRIDED, bool PADDED = false>
 struct LineRef {
     R* p0;
     R* p1;
     long long stride;
+    long long shift;
     int nmem;
     bool active;
     bool vec;  // strided pass moved as aligned 2-vectors
 
     __device__ __forceinline__ LineRef(const PassArgs& a, long long cl) {
         R* u = static_cast<R*>(a.u);
+        shift = a.out_shift;
         active = cl < a.clines;
         nmem = PADDED ? a.nmem : N;
         if (STRIDED) {
@@ -423,7 +426,7 @@ struct LineRef {
         constexpr int T = N / E;
         if (!active) return;
         if (STRIDED) {
-            R* q = p0 + t * stride;
+            R* q = p0 + shift + t * stride;
             const long long step = T * stride;
 #pragma unroll
             for (int e = 0; e < E; ++e, q += step) {
@@ -439,12 +442,14 @@ struct LineRef {
                 }
             }
         } else {
+            R* s0 = p0 + shift;
+            R* s1 = p1 ? p1 + shift : nullptr;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int idx = t + e * T;
                 if (PADDED && idx >= nmem) continue;
-                p0[idx] = x[e].x;
-                if (p1) p1[idx] = x[e].y;
+                s0[idx] = x[e].x;
+                if (s1) s1[idx] = x[e].y;
             }
         }
     }
@@ -799,6 +804,10 @@ cudaError_t launch_n(const PassArgs& a, cudaStream_t s) {
         // FP32: warp-local lines with 16 values per thread. Two warps per CTA
         // for long lines (few lines: many small CTAs spread better over 152
         // SMs), four otherwise.
+        // A strided pass that stores into mapped host memory: 256-thread CTAs
+        // of 256/T lines, so that each row a CTA writes is 64 bytes or more
+        // (the warp kernel's 16-byte pieces ran the link at a fraction of its rate).
+        if (a.host_io && a.inner > 1) return launch_cfg<R, N, 16, 256 / (N / 16), true, PADDED>(a, s);
         constexpr int WPB = N >= 512 ? 2 : 4;
         constexpr int LPW = 32 / (N / 16);
         // (not below N = 128: on the 64^2 grid one CTA of four 8-line warps was

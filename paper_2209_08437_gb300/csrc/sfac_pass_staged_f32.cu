@@ -274,7 +274,7 @@ int sm_count() {
 
 bool staged_pass_eligible(int N, const PassArgs& a) {
     const int bw = tile_width(N);
-    if (bw == 0 || a.nmem != N || a.inner <= 1) return false;
+    if (bw == 0 || a.nmem != N || a.inner <= 1 || a.host_io || a.out_shift != 0) return false;
     if (a.inner % 4 != 0 || a.inner < bw) return false;
     if (a.inner > 0x7fffffffLL || a.outer > 0x7fffffffLL) return false;
     if (reinterpret_cast<uintptr_t>(a.u) % 16 != 0) return false;

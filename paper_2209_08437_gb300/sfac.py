@@ -63,6 +63,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sfac_plan_kernel": (ctypes.c_int, [vp, ctypes.c_int, vp, P(ctypes.c_int)]),
         "sfac_plan_check": (ctypes.c_int, [vp, vp]),
         "sfac_plan_step_kernel": (ctypes.c_int, [vp, ll, P(ctypes.c_int)]),
+        "sfac_plan_host_route": (ctypes.c_int, [vp, vp, ll, P(ctypes.c_int)]),
         "sfac_plan_set_wait_limit": (ctypes.c_int, [vp, ll, ctypes.c_int]),
         "sfac_plan_tables": (ctypes.c_int, [P(SfacParams), ctypes.c_int, P(d), P(d), P(d), P(d)]),
         "sfac_batch_create": (ctypes.c_int, [P(SfacParams), ctypes.c_int, vp, P(vp)]),
@@ -201,6 +202,16 @@ def sfac_plan_step_kernel(plan: int, nsteps: int) -> int:
     kind = ctypes.c_int()
     _check(load().sfac_plan_step_kernel(plan, int(nsteps), ctypes.byref(kind)), "sfac_plan_step_kernel")
     return kind.value
+
+
+SFAC_HOST_COPY, SFAC_HOST_MAPPED, SFAC_HOST_MAPPED_IN = range(3)
+
+
+def sfac_plan_host_route(plan: int, u_host, nsteps: int) -> int:
+    """SFAC_HOST_* route that sfac_step_host takes for the host buffer u_host."""
+    route = ctypes.c_int()
+    _check(load().sfac_plan_host_route(plan, _ptr(u_host), int(nsteps), ctypes.byref(route)), "sfac_plan_host_route")
+    return route.value
 
 
 def sfac_plan_check(plan: int, stream=None) -> None:
@@ -539,6 +550,10 @@ class Plan:
     def kernel(self, axis: int, u) -> int:
         """SFAC_KERNEL_* that a pass along `axis` runs for the field u."""
         return sfac_plan_kernel(self.handle, axis, u)
+
+    def host_route(self, u_host, nsteps: int) -> int:
+        """SFAC_HOST_* route that step_host takes for the host buffer u_host."""
+        return sfac_plan_host_route(self.handle, u_host, nsteps)
 
     def step_kernel(self, nsteps: int) -> int:
         """SFAC_STEP_* that sfac_step uses for a call of nsteps steps."""

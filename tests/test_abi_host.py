@@ -88,6 +88,9 @@ def test_host_checks_of_the_newer_entry_points(lib):
     assert lib.sfac_probe_jq(S.SFAC_FP32, vp(16), vp(16), 4, 0.0, 1.0, None) == S.sfac.SFAC_EINVAL
     assert lib.sfac_probe_jq(S.SFAC_FP32, vp(16), vp(16), 4, 1.5, -0.5, None) == S.sfac.SFAC_EINVAL
     assert lib.sfac_probe_jq(S.SFAC_FP64, None, None, 0, 0.9, 0.1, None) == S.sfac.SFAC_OK
+    route = ctypes.c_int(9)
+    assert lib.sfac_plan_host_route(None, vp(16), 1, ctypes.byref(route)) == S.sfac.SFAC_EINVAL
+    assert route.value == 9
     assert lib.sfac_server_set_wait_limit(None, 10, -1) == S.sfac.SFAC_EINVAL
     launched = ctypes.c_int(7)
     assert lib.sfac_server_round(None, 4, 0, None, ctypes.byref(launched)) == S.sfac.SFAC_EINVAL
