@@ -78,18 +78,20 @@ PEAK_SOURCE = {"f64": "derived: 2 FP64 fma/clk/SM x 152 SMs x 2 flops x 2.07 GHz
                "f32": "derived: 128 FP32 lanes x 152 SMs x 2 flops x 2.07 GHz"}
 
 # DRAM bytes (read + write) per launch from ncu, keyed by (workload, precision,
-# axis): dram__bytes_read.sum + dram__bytes_write.sum of the captured launches
-# of each pass (the mean where several were captured), from
-#   ncu [--set full | --metrics dram__bytes_read.sum,dram__bytes_write.sum] --clock-control none
-#       -k regex:axis_pass -s <warm-up launches> -c <launches>
-#       python bench.py --steps 2 --warmup 3 --workload <w> --parity-steps 0 --no-cpu-baseline --no-extras
-# An entry is removed when its kernel changes.
+# axis): the mean of dram__bytes_read.sum + dram__bytes_write.sum over the
+# captured launches of each pass, from
+#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+#       -k regex:axis_pass [-s 15] -c <launches>
+#       python bench.py --workload <w> --steps 2 --warmup 3 --parity-steps 0 --no-cpu-baseline --no-extras
+# (-c 28 for 2d1024, -c 42 for 3d256, -s 15 -c 15 for 3d512). An entry is
+# removed when its kernel changes.
 NCU_TRAFFIC = {
-    ("2d1024", "f64", 0): 8592128, ("2d1024", "f64", 1): 8580864,
-    ("2d1024", "f32", 0): 4284598, ("2d1024", "f32", 1): 4285513,
-    ("3d256", "f64", 0): 208232704, ("3d256", "f64", 1): 213132544, ("3d256", "f64", 2): 213316096,
-    ("3d256", "f32", 0): 75255552, ("3d256", "f32", 1): 79353600, ("3d256", "f32", 2): 79172864,
-    ("3d512", "f32", 0): 1008508672, ("3d512", "f32", 1): 1014830250, ("3d512", "f32", 2): 1014986837,
+    ("2d1024", "f64", 0): 8570000, ("2d1024", "f64", 1): 8585714,
+    ("2d1024", "f32", 0): 4281429, ("2d1024", "f32", 1): 4291429,
+    ("3d256", "f64", 0): 203777143, ("3d256", "f64", 1): 209997143, ("3d256", "f64", 2): 209608571,
+    ("3d256", "f32", 0): 72635714, ("3d256", "f32", 1): 75765714, ("3d256", "f32", 2): 75717143,
+    ("3d512", "f64", 0): 2085800000, ("3d512", "f64", 1): 2090875000, ("3d512", "f64", 2): 2091510000,
+    ("3d512", "f32", 0): 1008836667, ("3d512", "f32", 1): 1014696667, ("3d512", "f32", 2): 1014876667,
 }
 
 
