@@ -215,12 +215,21 @@ def time_gpu_path(S, torch, problem, u0, prec, steps, warmup, flush):
     return {"step_ms": step_ms, "axis_ms": per_axis, "finite": ok, "launches": steps * d}
 
 
+HOST_ROUTES = {0: "copy: cudaMemcpyAsync in and out around the step",
+               1: "mapped: the first pass loads the field from the pinned host buffer over NVLink-C2C, "
+                  "the last pass stores the result into it",
+               2: "mapped in: the first pass loads the field from the pinned host buffer, a copy brings "
+                  "the result back"}
+
+
 def time_e2e(S, torch, problem, u0, prec, steps):
-    """The public host-memory entry point: H2D copy, one step, D2H copy per step."""
+    """The public host-memory entry point, one step per call: the field moves
+    from pinned host memory to the GPU and the result back in every call."""
     dt = torch.float64 if prec == S.SFAC_FP64 else torch.float32
     host = torch.tensor(u0, dtype=dt).pin_memory()
     arr = host.numpy()
     with S.Plan.for_problem(problem, prec) as plan:
+        route = plan.host_route(arr, 1)
         plan.step_host(arr, 1)      # allocates the staging buffer
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -229,7 +238,8 @@ def time_e2e(S, torch, problem, u0, prec, steps):
         el = time.perf_counter() - t0
     nbytes = arr.nbytes
     return {"value": problem.points * steps / el, "unit": UNIT,
-            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "call": "sfac_step_host(plan, pinned host field, 1)", "route": HOST_ROUTES.get(route, str(route))}
 
 
 def roofline(workload, problem, res, prec_name, peaks_live):
