@@ -237,9 +237,27 @@ def time_e2e(S, torch, problem, u0, prec, steps):
             plan.step_host(arr, 1)
         el = time.perf_counter() - t0
     nbytes = arr.nbytes
+    # The host link's own rate, for the bound it puts on this number: one
+    # pinned-host-to-device and one device-to-pinned-host copy of the field
+    # (cudaMemcpyAsync through torch), best of three each.
+    dev = torch.empty_like(host, device="cuda")
+    rates = {}
+    for name, src, dst in (("h2d", host, dev), ("d2h", dev, host)):
+        best = float("inf")
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dst.copy_(src, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        rates[name] = nbytes / best / 1e9
+    link_s = nbytes / (rates["h2d"] * 1e9) + nbytes / (rates["d2h"] * 1e9)
     return {"value": problem.points * steps / el, "unit": UNIT,
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-            "call": "sfac_step_host(plan, pinned host field, 1)", "route": HOST_ROUTES.get(route, str(route))}
+            "call": "sfac_step_host(plan, pinned host field, 1)", "route": HOST_ROUTES.get(route, str(route)),
+            "link_gbs": {"h2d": rates["h2d"], "d2h": rates["d2h"]},
+            "link_bound": problem.points / link_s}
 
 
 def roofline(workload, problem, res, prec_name, peaks_live):
