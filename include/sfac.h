@@ -192,7 +192,11 @@ sfac_status sfac_diagnostics(sfac_plan* plan, const void* u_dev, double* out, vo
  *                        result back.
  * Every route gives the same bits as sfac_step on a device field. Blocks until
  * the result is in u_host. The staging buffer is allocated on the first call
- * and kept by the plan. Not safe to call concurrently on one plan. */
+ * and kept by the plan. Not safe to call concurrently on one plan. Errors:
+ * SFAC_EINVAL (NULL plan or u_host, nsteps < 0), SFAC_ENOMEM (the staging
+ * buffer), SFAC_ECUDA (a copy, launch or synchronisation), SFAC_ETIMEOUT (a
+ * pass gave up a bounded wait, as sfac_plan_check reports; u_host then holds
+ * a field that is not valid). The paper has no counterpart. */
 sfac_status sfac_step_host(sfac_plan* plan, void* u_host, long long nsteps, void* stream);
 
 #define SFAC_HOST_COPY 0
@@ -206,8 +210,9 @@ sfac_status sfac_step_host(sfac_plan* plan, void* u_host, long long nsteps, void
  * the first and the last pass, so that the link's latency hides behind other
  * lines' work; otherwise SFAC_HOST_COPY. It is SFAC_HOST_MAPPED_IN for an FP32
  * plan whose last axis has an FFT length above 512 (whose pass would write
- * rows too narrow for the link). Host-only; nothing is enqueued. The paper has
- * no counterpart. */
+ * rows too narrow for the link). Host-only; nothing is enqueued. SFAC_EINVAL
+ * for a NULL plan, u_host or route, or nsteps < 0. The paper has no
+ * counterpart. */
 sfac_status sfac_plan_host_route(const sfac_plan* plan, const void* u_host, long long nsteps, int* route);
 
 /* Host-only: the FP64 tables sfac_plan_create computes for axis `axis` (0-based)
