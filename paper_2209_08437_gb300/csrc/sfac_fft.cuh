@@ -330,7 +330,7 @@ __device__ __forceinline__ void line_fft_tw(C2<R> (&x)[E], int t, const Tw& tws,
 }
 
 // ---------------------------------------------------------------------------
-// FP64 passes with ratio twiddles (FP64 lines of up to 1024 points, radix 8/4/2).
+// FP64 passes with ratio twiddles (FP64 lines of up to 2048 points, radix 8/4/2).
 //
 // The FP64 passes are bound by the FP64 pipe, so what counts is the number of
 // FP64 instructions. A twiddle w = c + i s is stored as c and the ratio

@@ -72,9 +72,11 @@ struct PassArgs {
 
 constexpr unsigned int SFAC_PASS_TIMEOUT = 1u;
 
-// Values per thread of the FP64 CTA pass for FFT length N. Lengths up to 1024
-// (E <= 8) run their FFTs with ratio twiddles.
-__host__ __device__ constexpr int f64_elems_per_thread(int N) { return N >= 2048 ? 16 : (N < 8 ? N : 8); }
+// Values per thread of the FP64 CTA pass for FFT length N. Lengths up to 2048
+// (E <= 8) run their FFTs with ratio twiddles; 4096-point lines take 16 values
+// (256 threads a line: 8 values would need 512 threads of about 180 registers,
+// more than an SM holds).
+__host__ __device__ constexpr int f64_elems_per_thread(int N) { return N >= 4096 ? 16 : (N < 8 ? N : 8); }
 
 // Launch one pass for line length N (a power of two in [4, 4096]).
 // Returns cudaErrorInvalidValue for an unsupported N.

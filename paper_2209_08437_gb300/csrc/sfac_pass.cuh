@@ -24,9 +24,9 @@
 //  - the TMA-staged kernel of sfac_pass_staged_f32.cu (FP32 strided axes) and
 //    the batch kernel of sfac_batch.cuh run the same warp-local lines.
 // The FP32 chain is the increment form, rolled for N <= SFAC_ROLLED_MAX_N.
-// The FP64 CTA kernel runs its FFTs on ratio twiddles for N <= 1024 (E <= 8;
+// The FP64 CTA kernel runs its FFTs on ratio twiddles for N <= 2048 (E <= 8;
 // FftPassRatio in sfac_fft.cuh, records in PassArgs::rtwid); the batch kernel
-// and lines of 2048+ points use the complex twiddle table.
+// and lines of 4096 points use the complex twiddle table.
 #pragma once
 
 #include <atomic>
@@ -680,10 +680,10 @@ axis_pass_warp_kernel(const PassArgs a0, long long ngroups) {
 // Launch configuration
 // ---------------------------------------------------------------------------
 
-// Elements per thread of kernel 1: 8 for most lengths (radix-8 passes), 16 from N = 2048.
+// Elements per thread of kernel 1: 8 for most lengths (radix-8 passes), 16 at N = 4096.
 template <int N>
 constexpr int elems_per_thread() {
-    return N >= 2048 ? 16 : (N < 8 ? N : 8);
+    return N >= 4096 ? 16 : (N < 8 ? N : 8);
 }
 
 // Per-kernel launch set-up, done once per device: the shared-memory attribute
