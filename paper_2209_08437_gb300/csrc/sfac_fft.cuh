@@ -330,7 +330,8 @@ __device__ __forceinline__ void line_fft_tw(C2<R> (&x)[E], int t, const Tw& tws,
 }
 
 // ---------------------------------------------------------------------------
-// FP64 passes with ratio twiddles (FP64 lines of up to 2048 points, radix 8/4/2).
+// FP64 passes with ratio twiddles (radix 8/4/2 for lines of up to 2048 points,
+// radix 16 for 4096).
 //
 // The FP64 passes are bound by the FP64 pipe, so what counts is the number of
 // FP64 instructions. A twiddle w = c + i s is stored as c and the ratio
@@ -353,6 +354,7 @@ __device__ __forceinline__ void line_fft_tw(C2<R> (&x)[E], int t, const Tw& tws,
 //                      c_2, c_1, c_1/sqrt 2, 0
 //   RAD 4 (8 values):  rho_1, rho_2, rho_3, c_2, c_3/c_1, c_1, 0, 0
 //   RAD 2 (2 values):  rho_1, c_1
+//   RAD 16 (36 values): as DftRatio16 below describes
 // Pass P = 1 has no twiddles and no records.
 
 __device__ __forceinline__ C2<double> cfma_d(double s, C2<double> u, C2<double> e) {
@@ -444,10 +446,92 @@ __device__ __forceinline__ void dft2_ratio(C2<double> (&a)[2], const double* __r
     a[1] = cfma_d(-rc.y, t1, a0);
 }
 
-// Doubles per record of a radix-RAD pass.
-constexpr int ratio_record(int rad) { return rad == 8 ? 16 : (rad == 4 ? 8 : 2); }
+// Radix 16 (FP64 lines of 4096 points, 16 values a thread). The same
+// bookkeeping, written once for every level of the radix-2 decimation in time
+// (Dft above): the node over the inputs R0 + S j (j < 16/S) returns its DFT
+// scaled by 1/c_R0; it combines its even half (scale c_R0) and its odd half
+// (scale c_{R0+S}) as u +- g W^s v with g = c_{R0+S}/c_R0 from the record.
+// W^s = 1 and -+i take g as it is; W^s = e^{-+i pi/4}, e^{-+3i pi/4} are
+// u/sqrt 2 and take h = g/sqrt 2; the other angles of the 16-point node
+// (odd multiples of pi/8) are k w with w = v turned and divided by
+// k = +-cos(pi/8) in two multiply-adds (the larger of the cosine and the sine,
+// ratio tan(pi/8) = sqrt 2 - 1 to the other), and take g cos(pi/8).
+// Record (36 doubles): rho_1..rho_15; g of node (S, R0) at 15 + S - 1 + R0 for
+// S = 1, 2, 4, 8; h of the nodes (1, 0), (2, 0), (2, 1) at 30..32;
+// g(1, 0) cos(pi/8) at 33; two doubles of padding.
+constexpr double kTanPi8 = 0.414213562373095048801688724209698;  // sqrt 2 - 1
 
-// The Stockham passes of FftPass with ratio twiddles (double, radix 2/4/8).
+// v e^{-+ 2 pi i q / 32} = k w for q in {2, 6, 10, 14}, |k| = cos(pi/8):
+// returns w; *neg says k < 0 (q = 14).
+template <bool INV>
+__device__ __forceinline__ C2<double> turn_pi8(C2<double> v, int q, bool* neg) {
+    *neg = (q == 14);
+    if (q == 2 || q == 14) {
+        // k = cos(2 pi q/32); ratio r = sin/cos = +tan(pi/8) (q = 2), -tan(pi/8) (q = 14)
+        const double r = q == 2 ? kTanPi8 : -kTanPi8;
+        return INV ? C2<double>{fma(-r, v.y, v.x), fma(r, v.x, v.y)} : C2<double>{fma(r, v.y, v.x), fma(-r, v.x, v.y)};
+    }
+    // q = 6, 10: k = sin(2 pi q/32) = cos(pi/8); ratio r = cos/sin = +tan(pi/8) (6), -tan(pi/8) (10)
+    const double r = q == 6 ? kTanPi8 : -kTanPi8;
+    return INV ? C2<double>{fma(r, v.x, -v.y), fma(r, v.y, v.x)} : C2<double>{fma(r, v.x, v.y), fma(r, v.y, -v.x)};
+}
+
+template <int M, int S, int R0, bool INV>
+struct DftRatio16 {
+    // x[j]: input R0 + S j carrying the scale c_{R0 + S j} (leaves already
+    // turned by 1 + i rho); on return the node's DFT with scale c_R0
+    static __device__ __forceinline__ void run(C2<double>* x, const double* __restrict__ p) {
+        C2<double> ev[M / 2], od[M / 2];
+#pragma unroll
+        for (int j = 0; j < M / 2; ++j) {
+            ev[j] = x[2 * j];
+            od[j] = x[2 * j + 1];
+        }
+        DftRatio16<M / 2, 2 * S, R0, INV>::run(ev, p);
+        DftRatio16<M / 2, 2 * S, R0 + S, INV>::run(od, p);
+        const double g = p[15 + S - 1 + R0];
+#pragma unroll
+        for (int s = 0; s < M / 2; ++s) {
+            const int q = s * (32 / M);
+            if (q == 0) {
+                x[s] = cfma_d(g, od[s], ev[s]);
+                x[s + M / 2] = cfma_d(-g, od[s], ev[s]);
+            } else if (q == 8) {
+                const C2<double> w = rot_quarter<INV>(od[s]);
+                x[s] = cfma_d(g, w, ev[s]);
+                x[s + M / 2] = cfma_d(-g, w, ev[s]);
+            } else if (q == 4 || q == 12) {
+                const double h = p[30 + (S - 1) + R0];
+                const C2<double> w = q == 4 ? rot_eighth_u<INV>(od[s]) : rot_3eighth_u<INV>(od[s]);
+                x[s] = cfma_d(h, w, ev[s]);
+                x[s + M / 2] = cfma_d(-h, w, ev[s]);
+            } else {
+                const double gk = p[33];
+                bool neg;
+                const C2<double> w = turn_pi8<INV>(od[s], q, &neg);
+                x[s] = cfma_d(neg ? -gk : gk, w, ev[s]);
+                x[s + M / 2] = cfma_d(neg ? gk : -gk, w, ev[s]);
+            }
+        }
+    }
+};
+template <int S, int R0, bool INV>
+struct DftRatio16<1, S, R0, INV> {
+    static __device__ __forceinline__ void run(C2<double>*, const double*) {}
+};
+
+// a_r <- sum_r w_r a_r e^{-+2 pi i r s / 16} with the twiddles of record p.
+template <bool INV>
+__device__ __forceinline__ void dft16_ratio(C2<double> (&a)[16], const double* __restrict__ p) {
+#pragma unroll
+    for (int r = 1; r < 16; ++r) a[r] = ratio_mul<INV>(a[r], p[r - 1]);
+    DftRatio16<16, 1, 0, INV>::run(a, p);
+}
+
+// Doubles per record of a radix-RAD pass.
+constexpr int ratio_record(int rad) { return rad == 16 ? 36 : (rad == 8 ? 16 : (rad == 4 ? 8 : 2)); }
+
+// The Stockham passes of FftPass with ratio twiddles (double, radix 2/4/8/16).
 // OFF: offset of this pass's records in the table.
 template <int N, int E, int P, int OFF, bool INV>
 struct FftPassRatio {
@@ -457,7 +541,7 @@ struct FftPassRatio {
     static constexpr int Q = E / RAD;
     static constexpr int REC = ratio_record(RAD);
     static constexpr int NEXT_OFF = OFF + (P > 1 ? P * REC : 0);
-    static_assert(RAD == 2 || RAD == 4 || RAD == 8, "ratio twiddles: radix 2, 4 or 8");
+    static_assert(RAD == 2 || RAD == 4 || RAD == 8 || RAD == 16, "ratio twiddles: radix 2, 4, 8 or 16");
 
     template <class Ex>
     static __device__ __forceinline__ void run(C2<double> (&x)[E], int t, const double* __restrict__ rt,
@@ -473,7 +557,8 @@ struct FftPassRatio {
                 Dft<double, RAD, INV>::run(a);
             } else {
                 const double* rec = rt + OFF + k * REC;
-                if constexpr (RAD == 8) dft8_ratio<INV>(a, rec);
+                if constexpr (RAD == 16) dft16_ratio<INV>(a, rec);
+                else if constexpr (RAD == 8) dft8_ratio<INV>(a, rec);
                 else if constexpr (RAD == 4) dft4_ratio<INV>(a, rec);
                 else dft2_ratio<INV>(a, rec);
             }

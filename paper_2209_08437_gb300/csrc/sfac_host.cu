@@ -247,7 +247,7 @@ std::vector<double> ratio_twiddles(int N, int E) {
         const int RAD = (P * E <= N) ? E : N / P;
         if (P > 1) {
             for (int k = 0; k < P; ++k) {
-                double c[8] = {}, s[8] = {}, rho[8] = {};
+                double c[16] = {}, s[16] = {}, rho[16] = {};
                 for (int r = 0; r < RAD; ++r) {
                     double cv, sv;
                     sincospi_frac(2LL * r * k, (long long)P * RAD, &cv, &sv);
@@ -255,7 +255,22 @@ std::vector<double> ratio_twiddles(int N, int E) {
                     s[r] = -sv;
                     rho[r] = s[r] / c[r];
                 }
-                if (RAD == 8) {
+                if (RAD == 16) {
+                    // DftRatio16 (sfac_fft.cuh): rho_1..rho_15; g(S, R0) = c_{R0+S}/c_R0
+                    // (c_0 = 1) at 15 + S - 1 + R0; h = g/sqrt 2 of the nodes (1,0),
+                    // (2,0), (2,1); g(1,0) cos(pi/8); padding
+                    double rec[36] = {};
+                    for (int r = 1; r < 16; ++r) rec[r - 1] = rho[r];
+                    for (int S = 1; S <= 8; S *= 2)
+                        for (int R0 = 0; R0 < S; ++R0)
+                            rec[15 + S - 1 + R0] = (R0 == 0 ? c[S] : c[R0 + S] / c[R0]);
+                    const long double rs2 = sqrtl(0.5L), cp8 = cosl(3.14159265358979323846264338327950288L / 8);
+                    rec[30] = (double)((long double)rec[15] * rs2);
+                    rec[31] = (double)((long double)rec[16] * rs2);
+                    rec[32] = (double)((long double)rec[17] * rs2);
+                    rec[33] = (double)((long double)rec[15] * cp8);
+                    out.insert(out.end(), rec, rec + 36);
+                } else if (RAD == 8) {
                     const double rec[16] = {rho[1], rho[2], rho[3], rho[4], rho[5], rho[6], rho[7], c[4],
                                             c[6] / c[2], c[5] / c[1], c[7] / c[3], c[3] / c[1],
                                             c[2], c[1], (double)((long double)c[1] * sqrtl(0.5L)), 0.0};

@@ -38,7 +38,7 @@ void compute_axis_padded(const AxisHost& T, double tau, AxisPadded* P);
 void compute_axis(double alpha, double eps, double tau, double a, double b, int n, AxisHost* T);
 
 // Ratio-twiddle records of the FP64 FFT passes of length N with E values per
-// thread (E <= 8; layout in sfac_fft.cuh, FftPassRatio); empty if no pass of
+// thread (E <= 16; layout in sfac_fft.cuh, FftPassRatio); empty if no pass of
 // span > 1 exists.
 std::vector<double> ratio_twiddles(int N, int E);
 

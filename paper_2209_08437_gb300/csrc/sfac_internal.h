@@ -33,7 +33,7 @@ sfac_status abi_exception_status() noexcept;
 //   increments the FP32 passes add; see sfac_pass.cuh)
 //  twist  = N complex e^{i pi k / N} (interleaved re, im)
 //  twid   = N complex e^{-2 pi i m / N}
-//  rtwid  = FP64 passes with E <= 8 values per thread: the ratio-twiddle
+//  rtwid  = FP64 CTA passes (E values per thread as below): the ratio-twiddle
 //           records of the FFT passes (sfac_fft.cuh, FftPassRatio)
 // J^Q_s(v) = v / sqrt(E + (1 - E) v^2) with E = e^{-2 s} is applied to every
 // value on load when jq_in != 0 and on store when jq_out != 0.
@@ -72,10 +72,10 @@ struct PassArgs {
 
 constexpr unsigned int SFAC_PASS_TIMEOUT = 1u;
 
-// Values per thread of the FP64 CTA pass for FFT length N. Lengths up to 2048
-// (E <= 8) run their FFTs with ratio twiddles; 4096-point lines take 16 values
-// (256 threads a line: 8 values would need 512 threads of about 180 registers,
-// more than an SM holds).
+// Values per thread of the FP64 CTA pass for FFT length N; its FFTs run on
+// ratio twiddles (radix 8/4/2, and radix 16 at 4096 points). 4096-point lines
+// take 16 values (256 threads a line: 8 values would need 512 threads of about
+// 180 registers, more than an SM holds).
 __host__ __device__ constexpr int f64_elems_per_thread(int N) { return N >= 4096 ? 16 : (N < 8 ? N : 8); }
 
 // Launch one pass for line length N (a power of two in [4, 4096]).

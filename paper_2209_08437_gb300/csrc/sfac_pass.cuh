@@ -24,9 +24,9 @@
 //  - the TMA-staged kernel of sfac_pass_staged_f32.cu (FP32 strided axes) and
 //    the batch kernel of sfac_batch.cuh run the same warp-local lines.
 // The FP32 chain is the increment form, rolled for N <= SFAC_ROLLED_MAX_N.
-// The FP64 CTA kernel runs its FFTs on ratio twiddles for N <= 2048 (E <= 8;
-// FftPassRatio in sfac_fft.cuh, records in PassArgs::rtwid); the batch kernel
-// and lines of 4096 points use the complex twiddle table.
+// The FP64 CTA kernel runs its FFTs on ratio twiddles (FftPassRatio in
+// sfac_fft.cuh, records in PassArgs::rtwid); the batch kernel uses the complex
+// twiddle table.
 #pragma once
 
 #include <atomic>
@@ -123,7 +123,7 @@ struct TwOf<float, N, E, true> {
     }
 };
 
-// The same with the FFTs on ratio twiddles (FP64, E <= 8; table rt).
+// The same with the FFTs on ratio twiddles (FP64, E <= 16; table rt).
 template <int N, int E, class Ex>
 __device__ __forceinline__ void apply_spectral_ratio(C2<double> (&x)[E], int t, const double* __restrict__ rt,
                                                      const Ex& ex, const double* __restrict__ m) {
@@ -162,7 +162,7 @@ __device__ __forceinline__ void zero_tail(C2<R> (&x)[E], int t, int nmem) {
 template <typename R, int N, int E, bool PADDED, bool RATIO, class Ex>
 __device__ __forceinline__ void two_level_chain(C2<R> (&x)[E], int t, const PassArgs& a, const Ex& ex) {
     constexpr int T = N / E;
-    static_assert(!RATIO || (sizeof(R) == 8 && E <= 8), "ratio twiddles: FP64, E <= 8");
+    static_assert(!RATIO || (sizeof(R) == 8 && E <= 16), "ratio twiddles: FP64, E <= 16");
     const Spectral<R, N, E, RATIO> sp{static_cast<const C2<R>*>(a.twid), static_cast<const double*>(a.rtwid)};
     if constexpr (PADDED) {
         sp.apply(x, t, ex, static_cast<const R*>(a.eC));
@@ -579,7 +579,7 @@ axis_pass_kernel(const PassArgs a) {
     C2<R> x[E];
     line.template load<E>(x, t);
     // ratio-twiddle records exist for the FP64 pass's default values per thread only
-    fused_pass<R, N, E, PADDED, (sizeof(R) == 8 && E <= 8 && E == f64_elems_per_thread(N))>(x, t, a, ex);
+    fused_pass<R, N, E, PADDED, (sizeof(R) == 8 && E <= 16 && E == f64_elems_per_thread(N))>(x, t, a, ex);
     line.template store<E>(x, t);
 }
 

@@ -97,7 +97,7 @@ struct sfac_plan {
         const void* eS;
         const void* twist;
         const void* twid;
-        const void* rtwid;  // FP64 ratio twiddles (E <= 8), else NULL
+        const void* rtwid;  // FP64 ratio twiddles (CTA passes), else NULL
         int fft_len;  // N of the pass: n, or the padded length L
         bool padded;
         // FP64 diagnostic tables: lambda/N, mu/N, twist, twiddles (padded axes:
@@ -360,14 +360,14 @@ sfac_status sfac_plan_create(const sfac_params* params, void* stream, sfac_plan*
         delete P;
         return cuda_fail(err, "cudaGetDevice");
     }
-    // FP64 ratio twiddles of each axis's FFT length (passes with E <= 8).
+    // FP64 ratio twiddles of each axis's FFT length.
     std::vector<double> rtw[3];
     if (params->prec == SFAC_FP64) {
         try {
             for (int l = 0; l < params->dim; ++l) {
                 const int N = padded[l] ? pad[l].L : params->n[l];
                 const int E = sfac::f64_elems_per_thread(N);
-                if (E <= 8) rtw[l] = sfac::ratio_twiddles(N, E);
+                if (E <= 16) rtw[l] = sfac::ratio_twiddles(N, E);
             }
         } catch (const std::bad_alloc&) {
             delete P;

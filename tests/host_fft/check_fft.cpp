@@ -3,7 +3,7 @@
 // barrier wherever the CTA would synchronise, against a long-double DFT.
 //  - complex twiddles, FP64 (E as the FP64 kernels) and FP32 (E = 16, on the
 //    packed two-lane FP32 forms, emulated lane by lane by the host shim);
-//  - ratio twiddles (FP64, E <= 8) with the table of ratio_twiddles; the table
+//  - ratio twiddles (FP64, every length) with the table of ratio_twiddles; the table
 //    is followed by poison values, so a record read past its end shows up as
 //    a wrong result;
 //  - FP32 with the per-thread twiddle rows of TwRows (built by build_tw_rows
@@ -92,7 +92,7 @@ void check(bool ratio) {
     }
     std::vector<double> rt;
     if (ratio) {
-        if constexpr (std::is_same<R, double>::value && E <= 8) {
+        if constexpr (std::is_same<R, double>::value && E <= 16) {
             rt = ratio_twiddles(N, E);
             size_t need = 0;
             for (int P = 1; P < N;) {
@@ -131,7 +131,7 @@ template <int N>
 void check_all() {
     constexpr int E64 = f64_elems_per_thread(N);
     check<double, N, E64>(false);
-    if constexpr (E64 <= 8) check<double, N, E64>(true);
+    check<double, N, E64>(true);
     if constexpr (N >= 32) check<float, N, 16>(false);
     // the other FP32 shapes: 8 values (batch kernel), N / 32 values (small grids)
     if constexpr (N >= 16 && N <= 512) check<float, N, 8>(false);
@@ -150,5 +150,6 @@ int main() {
     check_all<512>();
     check_all<1024>();
     check_all<2048>();
+    check_all<4096>();
     return 0;
 }

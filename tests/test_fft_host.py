@@ -1,9 +1,9 @@
 """The device FFT core (csrc/sfac_fft.cuh) compiled for the host and run by one
 host thread per GPU thread, meeting at a barrier wherever the CTA synchronises
-(tests/host_fft/check_fft.cpp). Every line length 4..2048 of the FP64 passes,
-forward and inverse, with complex twiddles and (E <= 8) with the ratio
-twiddles of the FP64 plan passes, and the FP32 radix-16 structure of lengths
-32..2048 on the packed two-lane FP32 forms the kernels use (emulated lane by
+(tests/host_fft/check_fft.cpp). Every line length 4..4096 of the FP64 passes,
+forward and inverse, with complex twiddles and with the ratio twiddles of the
+FP64 plan passes (radix 8/4/2, radix 16 at 4096), and the FP32 radix-16
+structure of lengths 32..4096 on the packed two-lane FP32 forms the kernels use (emulated lane by
 lane), against a long-double DFT.
 
 Bound: the error of a radix-2-based FFT grows like log2 N roundings, so the
@@ -47,11 +47,10 @@ def results(tmp_path_factory):
 
 def test_every_length_and_direction_is_covered(results):
     kinds = {(k, n, inv) for k, n, _, inv, _ in results}
-    for n in (4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048):
+    for n in (4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096):
         for inv in (0, 1):
             assert ("complex64b", n, inv) in kinds
-            if n <= 1024:
-                assert ("ratio64", n, inv) in kinds
+            assert ("ratio64", n, inv) in kinds
             if n >= 32:
                 assert ("complex32b", n, inv) in kinds
 

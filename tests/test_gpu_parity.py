@@ -34,7 +34,7 @@ def gpu_run(prob, u0, nsteps, prec=S.SFAC_FP64):
 
 
 SHAPES_2D = [(4, 4), (4, 8), (8, 4), (16, 16), (64, 32), (32, 128), (256, 256), (1024, 8),
-             (8, 1024), (2048, 4), (4, 2048), (4, 4096), (512, 16), (16, 512)]
+             (8, 1024), (2048, 4), (4, 2048), (4096, 2), (4, 4096), (512, 16), (16, 512)]
 SHAPES_3D = [(4, 4, 4), (4, 8, 16), (32, 4, 8), (16, 16, 16), (64, 8, 32)]
 
 
@@ -285,7 +285,7 @@ def test_fp32_error_against_fp64_oracle(which):
 # ---- lengths that are not powers of two (zero-padded convolution passes) -------
 
 ODD_SHAPES = [(63,), (2,), (3, 5), (100, 30), (63, 63), (64, 63), (63, 64), (255, 8), (7, 9, 11), (63, 16, 17),
-              (1000, 3), (3, 1000), (2048, 2)]
+              (1000, 3), (3, 1000), (1500, 2), (2, 1100), (2048, 2)]
 
 
 @pytest.mark.parametrize("n", ODD_SHAPES, ids=str)
