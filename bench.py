@@ -15,7 +15,7 @@ and per 100-step run), the 512-instance batched workload and the served
 Poisson request stream with its p50/p99 latency; and, under "peaks_measured",
 the multiply-add rates that a probe kernel reaches on this GPU.
 
-  python bench.py [--steps K] [--warmup W] [--workload 3d256|2d1024|2d64|3d512|batch512|serve]
+  python bench.py [--steps K] [--warmup W] [--workload 3d256|2d1024|2d64|3d512|2d4096|batch512|serve]
   python bench.py --impl reference      # the CPU FP64 oracle on the host cores
 """
 from __future__ import annotations
@@ -41,6 +41,7 @@ METRIC = "point-steps/s FP32 vs FP64 path at stated err vs oracle; served p50/p9
 UNIT = "point-steps/s"
 
 PROBE_3D512 = I.Problem(n=(512, 512, 512), alpha=(1.2, 1.5, 1.8), eps=0.08, tau=2e-3)
+PROBE_2D4096 = I.Problem(n=(4096, 4096), alpha=(1.3, 1.7), eps=0.05, tau=1e-3)
 
 WORKLOADS = {
     "3d256": dict(problem=I.CONFIG3, u0=I.config3_u0, parity_steps=3,
@@ -56,6 +57,10 @@ WORKLOADS = {
     "3d512": dict(problem=PROBE_3D512, u0=lambda: I.random_field(PROBE_3D512, 2, -1.0, 1.0), parity_steps=0,
                   name="3D SFAC n=512^3 (134,217,728 unknowns; HBM probe), alpha=(1.2,1.5,1.8), eps=0.08, "
                        "tau=2e-3, u0~U[-1,1] seed 2"),
+    # Long lines: 4096-point FFTs (radix 16), fields of 67 MB (FP32) and 134 MB (FP64).
+    "2d4096": dict(problem=PROBE_2D4096, u0=lambda: I.random_field(PROBE_2D4096, 1, -0.9, 0.9), parity_steps=0,
+                   name="2D SFAC n=4096^2 (16,777,216 unknowns; long-line probe), alpha=(1.3,1.7), eps=0.05, "
+                        "tau=1e-3, u0~U[-0.9,0.9] seed 1"),
 }
 
 
