@@ -15,8 +15,10 @@
 //
 // Kernel shapes that share that chain:
 //  - axis_pass_kernel: a line's T = N/E threads may span several warps, so the
-//    exchanges synchronise the CTA (FP64 at every N; FP32 below 32 and from
+//    exchanges synchronise the CTA (FP64 at every N; FP32 below 32 and at
 //    1024 points);
+//  - axis_pass_cta_rows_kernel: the same lines in persistent CTAs that keep
+//    the tables and twiddle rows in shared memory (FP32, 2048 and 4096 points);
 //  - axis_pass_warp_kernel: 16 values per thread, so a line of N <= 512 points
 //    lives inside one warp (with 32/T lines per warp); the exchanges need only
 //    warp-level synchronisation; persistent CTAs keep the tables in shared
@@ -676,6 +678,35 @@ axis_pass_warp_kernel(const PassArgs a0, long long ngroups) {
     }
 }
 
+// Persistent CTA lines (FP32 lines of 2048 and 4096 points): each CTA copies
+// the axis tables and builds the twiddle rows in shared memory once (up to
+// 205 KB at 4096 points), then takes the groups of LPC lines
+// blockIdx.x + k gridDim.x, lanes mapped as in axis_pass_kernel. Table and
+// twiddle loads from global memory had kept the LSU queue full there (ncu:
+// long-scoreboard and global-throttle stalls, l1tex 70% busy); the results are
+// bit-identical to axis_pass_kernel's.
+template <typename R, int N, int E, int LPC, bool STRIDED, bool PADDED>
+__global__ void __launch_bounds__(LPC * (N / E), 1)
+axis_pass_cta_rows_kernel(const PassArgs a0, long long ngroups) {
+    constexpr int T = N / E;
+    using Ex = PadExchange<R, N, LPC, STRIDED>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PassArgs a = a0;
+    SmemTables<R, N, E, PADDED>::load(a, smem_raw);
+    const int tid = threadIdx.x;
+    const int j = STRIDED ? (tid % LPC) : (tid / T);
+    const int t = STRIDED ? (tid / LPC) : (tid % T);
+    const Ex ex{reinterpret_cast<C2<R>*>(smem_raw + SmemTables<R, N, E, PADDED>::BYTES), j};
+    for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const LineRef<R, N, STRIDED, PADDED> line(a, g * LPC + j);
+        C2<R> x[E];
+        line.template load<E>(x, t);
+        fused_pass<R, N, E, PADDED, false, true>(x, t, a, ex);
+        line.template store<E>(x, t);
+        __syncthreads();  // the exchange region is reused by the next group
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Launch configuration
 // ---------------------------------------------------------------------------
@@ -763,6 +794,23 @@ cudaError_t launch_warp(const PassArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <typename R, int N, int E, int LPC, bool STRIDED, bool PADDED>
+cudaError_t launch_cta_rows(const PassArgs& a, cudaStream_t s) {
+    using Ex = PadExchange<R, N, LPC, STRIDED>;
+    const size_t smem = SmemTables<R, N, E, PADDED>::BYTES + sizeof(C2<R>) * (size_t)Ex::elems();
+    auto kern = axis_pass_cta_rows_kernel<R, N, E, LPC, STRIDED, PADDED>;
+    static LaunchSetup setup;
+    int dev = 0, resident = 0;
+    cudaError_t err = set_smem(kern, smem, setup, &dev);
+    if (err == cudaSuccess) err = resident_grid(kern, LPC * (N / E), smem, setup, dev, &resident);
+    if (err != cudaSuccess) return err;
+    const long long ngroups = (a.clines + LPC - 1) / LPC;
+    if (ngroups <= 0) return cudaSuccess;
+    const long long grid = ngroups < resident ? ngroups : resident;
+    kern<<<(unsigned)grid, LPC * (N / E), smem, s>>>(a, ngroups);
+    return cudaGetLastError();
+}
+
 // SMs of the current device (cached per device; 0 if unknown).
 inline int current_device_sms() {
     static std::atomic<int> cache[LaunchSetup::kMaxDevices] = {};
@@ -828,6 +876,14 @@ cudaError_t launch_n(const PassArgs& a, cudaStream_t s) {
         // 32-byte rows; the strided 1024-point pass went from 18.8 to 12.9 us
         // on a 1024^2 field).
         constexpr int LPC_S = (256 / (N / 16)) > 1 ? 256 / (N / 16) : 1;
+        // 2048 and 4096 points: persistent CTAs with the tables and twiddle
+        // rows in shared memory (side by side: 2D 4096^2 FP32 step 0.697 ->
+        // 0.437 ms, 2048^2 0.140 -> 0.107 ms). At 1024 points the grid is
+        // latency bound and the per-CTA table build cost more (0.036 -> 0.046 ms).
+        if constexpr (N >= 2048) {
+            if (a.inner > 1) return launch_cta_rows<R, N, 16, LPC_S, true, PADDED>(a, s);
+            return launch_cta_rows<R, N, 16, 1, false, PADDED>(a, s);
+        }
         if (a.inner > 1) return launch_cfg<R, N, 16, LPC_S, true, PADDED>(a, s);
         return launch_cfg<R, N, 16, 1, false, PADDED>(a, s);
     } else {
