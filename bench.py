@@ -88,7 +88,7 @@ PEAK_SOURCE = {"f64": "derived: 2 FP64 fma/clk/SM x 152 SMs x 2 flops x 2.07 GHz
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 #       -k regex:axis_pass [-s 15] -c <launches>
 #       python bench.py --workload <w> --steps 2 --warmup 3 --parity-steps 0 --no-cpu-baseline --no-extras
-# (-c 28 for 2d1024, -c 42 for 3d256, -s 15 -c 15 for 3d512). An entry is
+# (-c 28 for 2d1024 and 2d4096, -c 42 for 3d256, -s 15 -c 15 for 3d512). An entry is
 # removed when its kernel changes.
 NCU_TRAFFIC = {
     ("2d1024", "f64", 0): 8570000, ("2d1024", "f64", 1): 8585714,
@@ -97,6 +97,8 @@ NCU_TRAFFIC = {
     ("3d256", "f32", 0): 72635714, ("3d256", "f32", 1): 75765714, ("3d256", "f32", 2): 75717143,
     ("3d512", "f64", 0): 2085800000, ("3d512", "f64", 1): 2090875000, ("3d512", "f64", 2): 2091510000,
     ("3d512", "f32", 0): 1008836667, ("3d512", "f32", 1): 1014696667, ("3d512", "f32", 2): 1014876667,
+    ("2d4096", "f64", 0): 205950000, ("2d4096", "f64", 1): 213458571,
+    ("2d4096", "f32", 0): 71625714, ("2d4096", "f32", 1): 78167143,
 }
 
 
