@@ -8,7 +8,8 @@ points, a copy brings the result back (SFAC_HOST_MAPPED_IN); other fields,
 pageable buffers and the whole-call launch of small grids are copied in and
 out (SFAC_HOST_COPY). Every route runs the same arithmetic on the same lines
 as sfac_step on a device field, so the results must be the same bits, for
-every kernel route: FP64 CTA passes, FP32 warp and 1024-point CTA passes,
+every kernel route: FP64 CTA passes, FP32 warp, 1024-point CTA and
+2048-point persistent passes,
 zero-padded passes, and an FP32 last axis that the device route runs staged
 (TMA) and the mapped route on 256-thread CTAs (rows of 64 bytes or more)."""
 import numpy as np
@@ -29,6 +30,7 @@ CASES = [
     ((48, 256, 80), S.SFAC_FP32, MAPPED),       # zero-padded first and last axis
     ((1024, 64, 128), S.SFAC_FP32, MAPPED),     # 1024-point CTA pass first
     ((32, 256, 1024), S.SFAC_FP32, MAPPED_IN),  # 1024-point last axis: result copied back
+    ((2048, 16, 512), S.SFAC_FP32, MAPPED),     # 2048-point persistent CTAs read the host buffer
     ((256, 64), S.SFAC_FP64, COPY),             # 32 line pairs in the last pass
     ((64, 64), S.SFAC_FP32, COPY),              # small grid (whole-call launch from 2 steps)
     ((512,), S.SFAC_FP32, COPY),                # one line
