@@ -93,7 +93,7 @@ sfac_status sfac_plan_info(const sfac_plan* plan, int axis, int* fft_len, int* p
 
 /* Kernels of an axis pass (sfac_plan_kernel). The paper has no counterpart;
  * these describe only how libsfac maps the pass of Sec. 2.2 onto the GPU. */
-#define SFAC_KERNEL_CTA 0    /* lines spread over a CTA, CTA-wide exchanges (FP64; FP32 n >= 1024) */
+#define SFAC_KERNEL_CTA 0    /* lines spread over a CTA, CTA-wide exchanges (FP64; FP32 N >= 1024, persistent CTAs from 2048) */
 #define SFAC_KERNEL_WARP 1   /* FP32, 32 <= N <= 512: lines held inside one warp, persistent CTAs */
 #define SFAC_KERNEL_STAGED 2 /* the warp kernel fed by TMA tile copies (FP32 strided axes) */
 
